@@ -1,0 +1,173 @@
+"""Seeded synthetic radio-sky image pairs (input generator only).
+
+The paper evaluates on OSKAR-simulated GLEAM skies restored with Hogbom CLEAN
+(Section 3): a first epoch with 33 sources, and a second epoch with the 5
+faintest removed, at N = 2048, N_T = 64.  Those images are not available, so
+these generators stand in for them with the same shape: Gaussian-beam point
+sources (and, for the precision workload, extended Gaussian blobs) over
+Gaussian noise, a second epoch that drops the faintest sources and draws fresh
+noise, and an optional faint diffuse ripple common to both epochs.
+
+This module holds none of the method's arithmetic (no clamp, no sums, no
+ratios).  Both the CUDA path's tests and the oracle's tests take their inputs
+from here.
+
+Conventions
+-----------
+* Beam: FWHM F gives sigma_b = F / (2 sqrt(2 ln 2)); a source of flux f at a
+  continuous position is rendered as f * exp(-r^2 / (2 sigma^2)) (peak f,
+  Jy/beam), evaluated within +-6 sigma.
+* Noise: iid N(0, sigma^2) per pixel, an independent stream per epoch, so about
+  half of the noise pixels are negative and the clamp is exercised.
+* Seeds: ``np.random.default_rng([seed, stream, pair_index])`` with stream 0 =
+  sky, 1 = noise of epoch 1 (x), 2 = noise of epoch 2 (y).
+* Images are computed in FP64 and cast to the storage dtype at the end.
+"""
+import math
+
+import numpy as np
+
+FWHM_TO_SIGMA = 1.0 / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+
+
+def catalog(rng, N, n_src, flux_lo, flux_hi, fwhm, ext_frac=0.0,
+            ext_sigma=(5.0, 40.0)):
+    """Source list: positions uniform over the image, flux log-uniform in
+    [flux_lo, flux_hi]; a fraction ``ext_frac`` of sources are extended blobs
+    with sigma uniform in ``ext_sigma`` pixels, the rest beam-sized."""
+    px = rng.uniform(0.0, N, n_src)
+    py = rng.uniform(0.0, N, n_src)
+    flux = np.exp(rng.uniform(math.log(flux_lo), math.log(flux_hi), n_src))
+    sigma = np.full(n_src, fwhm * FWHM_TO_SIGMA)
+    if ext_frac > 0.0:
+        n_ext = int(round(ext_frac * n_src))
+        ext = rng.permutation(n_src)[:n_ext]
+        sigma[ext] = rng.uniform(ext_sigma[0], ext_sigma[1], n_ext)
+    return {"x": px, "y": py, "flux": flux, "sigma": sigma}
+
+
+def drop_faintest(cat, k):
+    """Second-epoch catalogue: the k lowest-flux sources removed (Section 3)."""
+    keep = np.argsort(cat["flux"], kind="stable")[k:]
+    keep.sort()
+    return {key: v[keep] for key, v in cat.items()}
+
+
+def render(cat, N):
+    """FP64 N x N image of the catalogue's Gaussian sources (row = y)."""
+    img = np.zeros((N, N), dtype=np.float64)
+    for sx, sy, f, s in zip(cat["x"], cat["y"], cat["flux"], cat["sigma"]):
+        h = int(math.ceil(6.0 * s))
+        i0, i1 = max(0, int(sy) - h), min(N, int(sy) + h + 1)
+        j0, j1 = max(0, int(sx) - h), min(N, int(sx) + h + 1)
+        if i0 >= i1 or j0 >= j1:
+            continue
+        ii = np.arange(i0, i1, dtype=np.float64)[:, None] - sy
+        jj = np.arange(j0, j1, dtype=np.float64)[None, :] - sx
+        img[i0:i1, j0:j1] += f * np.exp(-(ii * ii + jj * jj) / (2.0 * s * s))
+    return img
+
+
+def ripple(rng, N, amp):
+    """Faint diffuse background: three sinusoids with integer wave numbers 1-4
+    along each axis and random phases, scaled so that the peak is ``amp``."""
+    i = np.arange(N, dtype=np.float64)[:, None]
+    j = np.arange(N, dtype=np.float64)[None, :]
+    r = np.zeros((N, N))
+    for _ in range(3):
+        kx, ky = rng.integers(1, 5, 2)
+        ph = rng.uniform(0.0, 2.0 * math.pi)
+        r += np.sin(2.0 * math.pi * (kx * j + ky * i) / N + ph)
+    return r * (amp / np.max(np.abs(r)))
+
+
+def _cast(img, dtype):
+    if dtype in ("f32", np.float32):
+        return img.astype(np.float32)
+    if dtype in ("f16", np.float16):
+        return img.astype(np.float16)
+    if dtype == "bf16":
+        # round-to-nearest-even FP64 -> FP32 -> BF16 bit pattern, as uint16
+        f = img.astype(np.float32).view(np.uint32).astype(np.uint64)
+        rounded = (f + 0x7FFF + ((f >> 16) & 1)) >> 16
+        nan = np.isnan(img)
+        out = rounded.astype(np.uint16)
+        out[nan] = 0x7FC0
+        return out
+    raise ValueError("unknown dtype %r" % (dtype,))
+
+
+def sky_pair(N, *, n_src, flux=(0.005, 2.0), fwhm=4.0, noise=2e-4, n_drop=5,
+             ripple_amp=0.0, ext_frac=0.0, ext_sigma=(5.0, 40.0), seed=1,
+             pair_index=0, dtype="f32"):
+    """One (epoch 1, epoch 2) pair.  Epoch 2 drops the ``n_drop`` faintest
+    sources and draws fresh noise; the ripple is shared.  Returns (x, y) in the
+    storage dtype ("f32", "f16", or "bf16" as raw uint16 bit patterns)."""
+    rng_sky = np.random.default_rng([seed, 0, pair_index])
+    cat1 = catalog(rng_sky, N, n_src, flux[0], flux[1], fwhm, ext_frac, ext_sigma)
+    cat2 = drop_faintest(cat1, n_drop)
+    base = ripple(rng_sky, N, ripple_amp) if ripple_amp > 0 else 0.0
+    x = render(cat1, N) + base
+    y = render(cat2, N) + base
+    x += noise * np.random.default_rng([seed, 1, pair_index]).standard_normal((N, N))
+    y += noise * np.random.default_rng([seed, 2, pair_index]).standard_normal((N, N))
+    return _cast(x, dtype), _cast(y, dtype)
+
+
+# --- the paper-shaped workloads -------------------------------------------
+
+#: Small single pair: N=256, N_T=64, 10 sources (FWHM 3 px, flux log-uniform
+#: in [0.01, 1]), sigma 1e-3, the 3 faintest dropped, seed 0.
+SMALL_PAIR_N256 = dict(N=256, NT=64, n_src=10, flux=(0.01, 1.0), fwhm=3.0,
+                       noise=1e-3, n_drop=3, seed=0)
+
+#: Paper-scale pair (Section 3): N=2048, 33 sources (FWHM 4 px, flux
+#: log-uniform in [0.005, 2]), sigma 2e-4, diffuse ripple 1e-4, the 5 faintest
+#: dropped, seed 1.  N_T is swept over {16, 32, 64, 128, 256}; 64 is the paper's.
+PAPER_PAIR_N2048 = dict(N=2048, NT=64, n_src=33, flux=(0.005, 2.0), fwhm=4.0,
+                        noise=2e-4, n_drop=5, ripple_amp=1e-4, seed=1)
+PAPER_NT_SWEEP = (16, 32, 64, 128, 256)
+
+
+def small_pair(dtype="f32"):
+    w = dict(SMALL_PAIR_N256)
+    w.pop("NT")
+    return sky_pair(dtype=dtype, **w)
+
+
+def paper_pair(pair_index=0, dtype="f32", N=None):
+    w = dict(PAPER_PAIR_N2048)
+    w.pop("NT")
+    if N is not None:
+        w["n_src"] = max(1, int(round(33 * (N / 2048.0) ** 2)))
+        w["n_drop"] = max(1, int(math.ceil(0.1 * w["n_src"]))) if N != 2048 else 5
+        w["N"] = N
+    return sky_pair(pair_index=pair_index, dtype=dtype, **w)
+
+
+def mixed_batch_specs(n_pairs=64, seed=2):
+    """The batched workload's draw: N from {1024, 2048, 4096, 8192} with weights
+    4:3:2:1 and N_T from {32, 64, 128}, per pair.  Returns a list of (N, NT)."""
+    rng = np.random.default_rng([seed, 3])
+    Ns = rng.choice([1024, 2048, 4096, 8192], size=n_pairs,
+                    p=np.array([4, 3, 2, 1]) / 10.0)
+    NTs = rng.choice([32, 64, 128], size=n_pairs)
+    return [(int(a), int(b)) for a, b in zip(Ns, NTs)]
+
+
+def mixed_batch_pair(i, N, seed=2, dtype="f32"):
+    """Pair i of the batched workload: the paper-scale sky scaled to N, with
+    round(33 (N/2048)^2) sources and ceil(10%) of them dropped in epoch 2."""
+    n_src = max(1, int(round(33 * (N / 2048.0) ** 2)))
+    return sky_pair(N, n_src=n_src, flux=(0.005, 2.0), fwhm=4.0, noise=2e-4,
+                    n_drop=int(math.ceil(0.1 * n_src)), ripple_amp=1e-4,
+                    seed=seed, pair_index=i, dtype=dtype)
+
+
+def precision_pair(i, N=8192, seed=3, dtype="f32"):
+    """Pair i of the precision workload: 33 sources per pair, half point
+    sources (FWHM 4) and half extended blobs (sigma 5-40 px), peak flux
+    log-uniform in [1e-4, 1] (1e4 dynamic range), sigma 5e-3 noise, epoch 2
+    drops the faintest 10%.  Returns FP64-derived images in ``dtype``."""
+    return sky_pair(N, n_src=33, flux=(1e-4, 1.0), fwhm=4.0, noise=5e-3,
+                    n_drop=4, ext_frac=0.5, seed=seed, pair_index=i, dtype=dtype)
