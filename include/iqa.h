@@ -1,0 +1,200 @@
+/*
+ * iqa.h -- C ABI of libiqa: tile-wise LISI / augLISI image-quality maps on GB300.
+ *
+ * Method (arxiv 2501.10653, "GPU Accelerated Image Quality Assessment-Based
+ * Software for Transient Detection"):
+ *   Section 2   negative pixels of both N x N images are set to zero; the images
+ *               are cut into N_T x N_T tiles; every tile gets one value.
+ *   Eq. 1       lisi_t = D * A_t / (max(Sx_t, Sy_t) + C2)
+ *   Eq. 2       auglisi_t = 1 - B_t / (Sx_t + Sy_t + C)
+ *   with, over the clamped pixels of tile t,
+ *               A_t  = sum |x+y| / (|x-y| + C1)      B_t  = sum |x+y| |x-y|
+ *               Sx_t = sum x                         Sy_t = sum y
+ *   Section 3   the per-tile values form the IQA matrix, one entry per tile.
+ *
+ * Conventions shared by every entry point
+ *   - Images are N x N, row-major, contiguous (row stride N elements).  Tile t
+ *     is at tile-row r = t / (N/N_T), tile-column c = t % (N/N_T), rows in
+ *     memory order.  Maps are (N/N_T) x (N/N_T) float32, row-major, entry t.
+ *   - The clamp is "v > 0 ? v : 0": NaN and -0 read as 0.  Inputs are never
+ *     written: the clamp happens as pixels are loaded.
+ *   - Per-tile sums, where requested, are float64 [n][4] = (A, B, Sx, Sy).
+ *   - Device-pointer calls are stream-ordered: they validate, enqueue on the
+ *     given stream and return without synchronising.  The stream must belong
+ *     to the context's device, and that device must be current.
+ *   - Nothing throws across the ABI: every call returns an iqa_status, and
+ *     iqa_last_error() gives a one-line reason for the latest failure.
+ *   - The caller owns every buffer it passes; the context owns its workspace.
+ *   - A context may be used from several host threads; calls are serialised
+ *     internally where they touch context state.
+ */
+#ifndef IQA_H
+#define IQA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL means the legacy default stream. */
+typedef struct CUstream_st *iqa_stream;
+
+typedef enum {
+    IQA_OK = 0,
+    IQA_PENDING = 1,           /* iqa_poll: request not finished yet          */
+    IQA_ERR_INVALID_ARG = -1,  /* bad shape, pointer, dtype or constant       */
+    IQA_ERR_NOMEM = -2,        /* workspace does not fit the HBM budget       */
+    IQA_ERR_CUDA = -3,         /* a CUDA call failed (text in last_error)     */
+    IQA_ERR_TIMEOUT = -4,      /* a bounded wait ran out                      */
+    IQA_ERR_BUSY = -5,         /* queue or slot table full                    */
+    IQA_ERR_UNSUPPORTED = -6   /* valid request this build cannot serve       */
+} iqa_status;
+
+/* Pixel storage type of both input images. */
+typedef enum {
+    IQA_F32 = 0,
+    IQA_F16 = 1,
+    IQA_BF16 = 2
+} iqa_dtype;
+
+/*
+ * Constants of Eq. 1 and Eq. 2.  Section 1 only says C1, C2, C << 1 and never
+ * defines D.  Defaults (iqa_default_params): C1 = C2 = C = 1e-6 and D = C1/2,
+ * the value for which identical inputs give LISI -> 1 and every LISI lies in
+ * [0, 1].  D <= 0 on input means "use C1/2".  Requirements: C1 > 0, C2 >= 0,
+ * C >= 0, all finite.
+ */
+typedef struct {
+    double C1;
+    double C2;
+    double C;
+    double D;
+} iqa_params;
+
+typedef struct iqa_ctx iqa_ctx;
+
+/* Library version, e.g. "iqa 0.1.0 sm_103a". */
+const char *iqa_version(void);
+
+/* Fills *p with the defaults above.  Returns IQA_ERR_INVALID_ARG if p is NULL. */
+iqa_status iqa_default_params(iqa_params *p);
+
+/*
+ * Creates a context on CUDA device `device`.  hbm_budget_bytes caps the device
+ * memory the context may allocate for its own workspace (0 = no cap).  On
+ * success *out owns the context; free it with iqa_destroy.
+ * Errors: IQA_ERR_INVALID_ARG (out NULL, bad device), IQA_ERR_CUDA.
+ */
+iqa_status iqa_create(iqa_ctx **out, int device, size_t hbm_budget_bytes);
+
+/* Frees the context and its workspace after waiting for its own streams.
+ * NULL is ignored. */
+void iqa_destroy(iqa_ctx *ctx);
+
+/*
+ * One-line reason for the latest failed call on ctx (or of iqa_create when
+ * ctx is NULL).  The string belongs to the library and stays valid until the
+ * next call on the same context.
+ */
+const char *iqa_last_error(const iqa_ctx *ctx);
+
+/*
+ * LISI map (Eq. 1) of the tiles of x and y, from one read of each pixel.
+ *   x, y      device pointers, N*N elements of `dtype`, row-major
+ *   N, NT     image side and tile side; NT must divide N
+ *   params    constants (NULL = defaults)
+ *   map       device pointer, (N/NT)^2 float32, written entry t = r*(N/NT)+c
+ *   sums      device pointer or NULL; if given, (N/NT)^2 x 4 float64
+ *             (A, B, Sx, Sy) per tile
+ *   stream    stream to enqueue on
+ * Errors: IQA_ERR_INVALID_ARG (NULL input or map, N < 1, NT < 1, N % NT != 0,
+ * bad dtype, bad constants), IQA_ERR_CUDA (launch failed).
+ */
+iqa_status iqa_lisi(iqa_ctx *ctx, const void *x, const void *y, iqa_dtype dtype,
+                    int N, int NT, const iqa_params *params, float *map,
+                    double *sums, iqa_stream stream);
+
+/* augLISI map (Eq. 2); arguments and errors as for iqa_lisi. */
+iqa_status iqa_auglisi(iqa_ctx *ctx, const void *x, const void *y,
+                       iqa_dtype dtype, int N, int NT, const iqa_params *params,
+                       float *map, double *sums, iqa_stream stream);
+
+/*
+ * Both maps from the same single read of each pixel (Eq. 1 and Eq. 2 share the
+ * clamp, |x+y|, |x-y| and the pixel sums).  lisi_map or aug_map may be NULL to
+ * skip that map, but not both (unless sums is given).  Other arguments and
+ * errors as for iqa_lisi.
+ */
+iqa_status iqa_both(iqa_ctx *ctx, const void *x, const void *y, iqa_dtype dtype,
+                    int N, int NT, const iqa_params *params, float *lisi_map,
+                    float *aug_map, double *sums, iqa_stream stream);
+
+/*
+ * End-to-end form of iqa_both for images in HOST memory (Section 2's
+ * interface: images in, IQA matrix out).  The context copies the images to
+ * its device workspace in row bands on one of its own streams and computes
+ * each band as soon as it lands, so copies and kernels overlap; the maps (and
+ * sums) are copied back to host memory.  Page-locked host buffers give full
+ * copy bandwidth; pageable ones work but are slower.  Synchronous: returns
+ * when the host outputs are written.
+ *   hx, hy               host pointers, N*N elements of dtype
+ *   lisi_map, aug_map    host pointers, (N/NT)^2 float32 each, either NULL
+ *   sums                 host pointer or NULL, (N/NT)^2 x 4 float64
+ * Errors: as iqa_both, plus IQA_ERR_NOMEM when 2*N*N elements of workspace do
+ * not fit the context's HBM budget.
+ */
+iqa_status iqa_both_host(iqa_ctx *ctx, const void *hx, const void *hy,
+                         iqa_dtype dtype, int N, int NT,
+                         const iqa_params *params, float *lisi_map,
+                         float *aug_map, double *sums);
+
+/*
+ * Launch shape of the tile kernel for one (dtype, N, NT, maps) key.  The paper
+ * gives each tile one thread block (Section 2); here a CTA streams a "unit" of
+ * `tiles_across` whole tiles side by side, or 1/`split` of one tile's rows,
+ * with the `split` CTAs of a tile forming a thread-block cluster that combines
+ * its partial sums in distributed shared memory.
+ *   threads        128, 256 or 512 threads per CTA
+ *   ilp            2, 4 or 8: 16-byte loads of each image in flight per thread
+ *   tiles_across   whole tiles per CTA (divides N/NT, <= 64)
+ *   split          CTAs per tile (divides NT, <= 8); split > 1 needs
+ *                  tiles_across == 1
+ *   vector         1: 16-byte loads (needs 16-byte aligned images and NT a
+ *                  multiple of 16 bytes); 0: scalar loads, 256 threads, ilp 8
+ *   variant        0: the streaming-load kernel
+ * maps: 1 = LISI only, 2 = augLISI only, 3 = both (also used when sums are
+ * requested).
+ */
+typedef struct {
+    int threads;
+    int ilp;
+    int tiles_across;
+    int split;
+    int vector;
+    int variant;
+} iqa_launch_config;
+
+/*
+ * The launch shape the next call for this key would use with 16-byte aligned
+ * inputs: the pinned (or autotuned) one if any, else the built-in heuristic.
+ * Errors: IQA_ERR_INVALID_ARG.
+ */
+iqa_status iqa_get_config(iqa_ctx *ctx, iqa_dtype dtype, int N, int NT, int maps,
+                          iqa_launch_config *out);
+
+/*
+ * Pins a launch shape for this key (cfg == NULL removes the pin).  Results do
+ * not depend on the shape beyond FP32 summation order.
+ * Errors: IQA_ERR_INVALID_ARG (shape not valid for this key; reason in
+ * iqa_last_error), IQA_ERR_UNSUPPORTED (variant not built).
+ */
+iqa_status iqa_set_config(iqa_ctx *ctx, iqa_dtype dtype, int N, int NT, int maps,
+                          const iqa_launch_config *cfg);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IQA_H */

@@ -1,0 +1,59 @@
+// iqa_ctx.h -- the context object behind the opaque iqa_ctx handle.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "iqa.h"
+#include "iqa_internal.h"
+
+struct iqa_ctx {
+    int device = 0;
+    size_t budget = 0;  // 0 = no cap on the context's own allocations
+    int num_sms = 0;
+    int l2_bytes = 0;
+    int cc_major = 0, cc_minor = 0;
+
+    std::mutex err_mu;
+    std::string last_error;
+
+    // launch shapes pinned by iqa_set_config or chosen by the autotuner,
+    // keyed by (dtype, N, NT, maps)
+    std::mutex cfg_mu;
+    std::map<std::tuple<int, int, int, int>, iqa::TileConfig> pinned;
+
+    // workspace of the host-buffer path (iqa_both_host)
+    std::mutex host_mu;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t s_copy = nullptr;
+    cudaStream_t s_comp = nullptr;
+    std::vector<cudaEvent_t> band_events;
+};
+
+namespace iqa {
+
+void set_error(iqa_ctx *ctx, const char *fmt, ...);
+iqa_status cuda_fail(iqa_ctx *ctx, cudaError_t e, const char *what);
+int elem_size(iqa_dtype d);
+bool dtype_ok(int d);
+iqa_status resolve_params(iqa_ctx *ctx, const iqa_params *in, iqa_params *out);
+iqa_status check_shape(iqa_ctx *ctx, int N, int NT);
+bool config_valid(int N, int NT, iqa_dtype dtype, const TileConfig &c,
+                  std::string *why);
+TileConfig default_config(int N, int NT, iqa_dtype dtype, bool aligned,
+                          int num_sms);
+TileConfig pick_config(iqa_ctx *ctx, int N, int NT, iqa_dtype dtype, int maps,
+                       bool aligned);
+cudaError_t launch_tiles(const TileArgs &p, const TileConfig &c, iqa_dtype dtype,
+                         int maps, int rows, cudaStream_t st);
+TileArgs make_args(const void *x, const void *y, int N, int NT,
+                   const TileConfig &c, const iqa_params &P, float *lisi,
+                   float *aug, double *sums);
+
+}  // namespace iqa

@@ -1,0 +1,347 @@
+// iqa_device.cuh -- device building blocks of the tile-wise LISI / augLISI maps.
+//
+// arxiv 2501.10653, Section 2: negative pixels are set to zero, the images are
+// cut into N_T x N_T tiles, and each tile reduces, over its clamped pixels,
+//   A  = sum |x+y| / (|x-y| + C1)   (numerator sum of Eq. 1)
+//   B  = sum |x+y| |x-y|            (numerator sum of Eq. 2)
+//   Sx = sum x,  Sy = sum y         (denominators of Eq. 1 and Eq. 2)
+// The paper names this pixel summation as the expensive step and gives it one
+// thread block per tile with a shared-memory reduction.  Here a CTA streams a
+// "unit": a rectangle of RH rows and TX whole tiles across (or, with a cluster
+// of S CTAs along y, 1/S of one tile's rows), with 16-byte non-caching loads,
+// the clamp and every term fused into that single read, per-thread FP32 sums
+// folded with Kahan compensation, and an FP32 shuffle-tree / cross-CTA combine.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace iqa {
+
+// ---------------------------------------------------------------------------
+// Launch arguments shared by the host launchers and the kernels.
+struct TileArgs {
+    const void *x;
+    const void *y;
+    long long N;        // image side = row stride in elements
+    int NT;             // tile side
+    int T;              // tiles per image row = N / NT
+    int TX;             // whole tiles across one unit
+    int S;              // CTAs per tile along y (cluster size), RH = NT / S
+    int RH;             // rows per unit
+    int LPU;            // vectors per unit row = TX * NT / VEC
+    int LPT;            // vectors per tile row = NT / VEC
+    int tile_row0;      // first tile row covered by this launch
+    float C1f;          // C1 rounded to float, used in the per-pixel divide
+    float C2f, Cf, Df;  // Eq. 1 / Eq. 2 constants for the per-tile combine
+    float *lisi;        // (T*T) map or nullptr
+    float *aug;         // (T*T) map or nullptr
+    double *sums;       // (T*T*4) or nullptr
+};
+
+// ---------------------------------------------------------------------------
+// Loads.  16-byte vector loads through the non-coherent path without L1
+// allocation (every pixel is read exactly once), with a 256-byte L2 prefetch
+// hint that matches the row segments of a tile.
+__device__ __forceinline__ uint4 ld_stream16(const void *p)
+{
+    uint4 r;
+    asm("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t ld_stream4(const void *p)
+{
+    uint32_t r;
+    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(r) : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t ld_stream2(const void *p)
+{
+    unsigned short r;
+    asm("ld.global.nc.L1::no_allocate.u16 %0, [%1];" : "=h"(r) : "l"(p));
+    return (uint32_t)r;
+}
+
+// Storage types: VEC elements per 16-byte vector.
+template <typename T> struct Elem;
+template <> struct Elem<float> { static constexpr int VEC = 4; };
+template <> struct Elem<__half> { static constexpr int VEC = 8; };
+template <> struct Elem<__nv_bfloat16> { static constexpr int VEC = 8; };
+
+// Raw register form of VEC elements (VEC == full vector, or 1 = scalar path).
+template <typename T, int VEC> struct Raw { uint4 v; };
+template <typename T> struct Raw<T, 1> { uint32_t v; };
+
+template <typename T, int VEC>
+__device__ __forceinline__ Raw<T, VEC> load_raw(const T *p)
+{
+    Raw<T, VEC> r;
+    if constexpr (VEC == 1) {
+        if constexpr (sizeof(T) == 4) r.v = ld_stream4(p);
+        else r.v = ld_stream2(p);
+    } else {
+        r.v = ld_stream16(p);
+    }
+    return r;
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ Raw<T, VEC> zero_raw()
+{
+    Raw<T, VEC> r;
+    if constexpr (VEC == 1) r.v = 0u;
+    else r.v = make_uint4(0u, 0u, 0u, 0u);
+    return r;
+}
+
+__device__ __forceinline__ void h2_to_f(uint32_t w, float &lo, float &hi)
+{
+    __half2 h = *reinterpret_cast<__half2 *>(&w);
+    float2 f = __half22float2(h);
+    lo = f.x;
+    hi = f.y;
+}
+
+__device__ __forceinline__ void b2_to_f(uint32_t w, float &lo, float &hi)
+{
+    lo = __uint_as_float(w << 16);
+    hi = __uint_as_float(w & 0xffff0000u);
+}
+
+// Widen VEC stored elements to float (exact for all three storage types).
+template <typename T, int VEC>
+__device__ __forceinline__ void unpack(const Raw<T, VEC> &r, float (&f)[VEC])
+{
+    if constexpr (VEC == 1) {
+        if constexpr (sizeof(T) == 4) {
+            f[0] = __uint_as_float(r.v);
+        } else if constexpr (std::is_same<T, __half>::value) {
+            __half h = __ushort_as_half((unsigned short)r.v);
+            f[0] = __half2float(h);
+        } else {
+            f[0] = __uint_as_float(r.v << 16);
+        }
+    } else if constexpr (sizeof(T) == 4) {
+        f[0] = __uint_as_float(r.v.x);
+        f[1] = __uint_as_float(r.v.y);
+        f[2] = __uint_as_float(r.v.z);
+        f[3] = __uint_as_float(r.v.w);
+    } else if constexpr (std::is_same<T, __half>::value) {
+        h2_to_f(r.v.x, f[0], f[1]);
+        h2_to_f(r.v.y, f[2], f[3]);
+        h2_to_f(r.v.z, f[4], f[5]);
+        h2_to_f(r.v.w, f[6], f[7]);
+    } else {
+        b2_to_f(r.v.x, f[0], f[1]);
+        b2_to_f(r.v.y, f[2], f[3]);
+        b2_to_f(r.v.z, f[4], f[5]);
+        b2_to_f(r.v.w, f[6], f[7]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-pixel terms of Eq. 1 / Eq. 2 for VEC pixel pairs, summed pairwise.
+// Clamp: fmaxf(v, 0) returns 0 for v <= 0 and for NaN (the non-NaN operand).
+// With both pixels clamped, |x + y| = x + y.  The divide uses the fast
+// reciprocal-based __fdividef (<= 2 ulp for the denominators that occur here,
+// |x-y| + C1 in [C1, 2^126]).
+template <int VEC, bool DO_A, bool DO_B>
+__device__ __forceinline__ void pixel_terms(const float (&xv)[VEC],
+                                            const float (&yv)[VEC], float C1f,
+                                            float &a, float &b, float &sx,
+                                            float &sy)
+{
+    float ta[VEC], tb[VEC], tx[VEC], ty[VEC];
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) {
+        float xc = fmaxf(xv[i], 0.0f);
+        float yc = fmaxf(yv[i], 0.0f);
+        float s = xc + yc;
+        float d = fabsf(xc - yc);
+        ta[i] = DO_A ? __fdividef(s, d + C1f) : 0.0f;
+        tb[i] = DO_B ? s * d : 0.0f;
+        tx[i] = xc;
+        ty[i] = yc;
+    }
+#pragma unroll
+    for (int w = VEC / 2; w >= 1; w >>= 1) {
+#pragma unroll
+        for (int i = 0; i < w; ++i) {
+            if (DO_A) ta[i] += ta[i + w];
+            if (DO_B) tb[i] += tb[i + w];
+            tx[i] += tx[i + w];
+            ty[i] += ty[i + w];
+        }
+    }
+    a = ta[0];
+    b = tb[0];
+    sx = tx[0];
+    sy = ty[0];
+}
+
+// Kahan-compensated float accumulator.
+struct Kahan {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float v)
+    {
+        float yv = v - c;
+        float t = s + yv;
+        c = (t - s) - yv;
+        s = t;
+    }
+    __device__ __forceinline__ float value() const { return s - c; }
+};
+
+// ---------------------------------------------------------------------------
+// Streams one unit (RH rows x LPU vectors, top-left at xu / yu, row stride N)
+// and returns this thread's four sums.  Vector v = tid + j * THREADS of the
+// unit is (row v / LPU, column v % LPU); (row, column) advance incrementally.
+// ILP vectors of each image are in flight per thread before any is used.
+template <typename T, int VEC, int ILP, int THREADS, bool DO_A, bool DO_B>
+__device__ __forceinline__ void accumulate_unit(const T *__restrict__ xu,
+                                                const T *__restrict__ yu,
+                                                long long N, int RH, int LPU,
+                                                float C1f, float (&acc)[4])
+{
+    const int tid = threadIdx.x;
+    int row = tid / LPU;
+    int col = tid - row * LPU;
+    const int drow = THREADS / LPU;
+    const int dcol = THREADS - drow * LPU;
+    Kahan ka, kb, kx, ky;
+    while (row < RH) {
+        Raw<T, VEC> rx[ILP], ry[ILP];
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+            if (row < RH) {
+                long long off = (long long)row * N + (long long)col * VEC;
+                rx[u] = load_raw<T, VEC>(xu + off);
+                ry[u] = load_raw<T, VEC>(yu + off);
+            } else {
+                rx[u] = zero_raw<T, VEC>();
+                ry[u] = zero_raw<T, VEC>();
+            }
+            col += dcol;
+            row += drow;
+            if (col >= LPU) {
+                col -= LPU;
+                row += 1;
+            }
+        }
+        float ba = 0.0f, bb = 0.0f, bx = 0.0f, by = 0.0f;
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+            float xv[VEC], yv[VEC];
+            unpack<T, VEC>(rx[u], xv);
+            unpack<T, VEC>(ry[u], yv);
+            float a, b, sx, sy;
+            // a vector that was not loaded is all zeros and adds exactly 0
+            pixel_terms<VEC, DO_A, DO_B>(xv, yv, C1f, a, b, sx, sy);
+            ba += a;
+            bb += b;
+            bx += sx;
+            by += sy;
+        }
+        if (DO_A) ka.add(ba);
+        if (DO_B) kb.add(bb);
+        kx.add(bx);
+        ky.add(by);
+    }
+    acc[0] = ka.value();
+    acc[1] = kb.value();
+    acc[2] = kx.value();
+    acc[3] = ky.value();
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Cross-thread reduction of one unit, in FP32 (the low-rate FP64 pipe of this
+// GPU is kept off the per-unit path).  part[tl * 4 + k] receives tile tl's sum
+// k (A, B, Sx, Sy).
+//  * TX == 1: every warp reduces its lanes with an xor-shuffle tree, then warp
+//    0 combines the per-warp partials the same way.
+//  * TX > 1: the host guarantees THREADS % LPU == 0, so a thread's column and
+//    hence its tile is fixed; the threads of tile tl are q * LPU + tl * LPT + e
+//    (q < THREADS / LPU, e < LPT).  Their sums go through shared memory; warp
+//    w owns tiles w, w + warps, ... and sums its share lane-wise in a fixed
+//    order, then with a shuffle tree.
+template <int THREADS>
+__device__ __forceinline__ void reduce_unit(const float (&acc)[4], int TX,
+                                            int LPU, int LPT,
+                                            float (*red)[THREADS],
+                                            float *part)
+{
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    constexpr int WARPS = THREADS / 32;
+    if (TX == 1) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float v = warp_sum(acc[k]);
+            if (lane == 0) red[k][warp] = v;
+        }
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float v = lane < WARPS ? red[k][lane] : 0.0f;
+                v = warp_sum(v);
+                if (lane == 0) part[k] = v;
+            }
+        }
+        __syncthreads();
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[k][tid] = acc[k];
+    __syncthreads();
+    const int count = (THREADS / LPU) * LPT;
+    for (int tl = warp; tl < TX; tl += WARPS) {
+        float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int e = lane; e < count; e += 32) {
+            int q = e / LPT;
+            int src = q * LPU + tl * LPT + (e - q * LPT);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s[k] += red[k][src];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float v = warp_sum(s[k]);
+            if (lane == 0) part[tl * 4 + k] = v;
+        }
+    }
+    __syncthreads();
+}
+
+// Eq. 1 / Eq. 2 per-tile combine and the output writes.  IEEE float division
+// (correctly rounded): with nonnegative sums the ratios carry a few float
+// roundings, far inside the 1e-5 per-tile bound; the optional sums are
+// exported widened to FP64.
+__device__ __forceinline__ void write_tile(const TileArgs &p, long long t,
+                                           float A, float B, float Sx, float Sy)
+{
+    if (p.lisi) p.lisi[t] = __fdiv_rn(p.Df * A, fmaxf(Sx, Sy) + p.C2f);
+    if (p.aug) p.aug[t] = 1.0f - __fdiv_rn(B, (Sx + Sy) + p.Cf);
+    if (p.sums) {
+        double *o = p.sums + 4 * t;
+        o[0] = A;
+        o[1] = B;
+        o[2] = Sx;
+        o[3] = Sy;
+    }
+}
+
+}  // namespace iqa

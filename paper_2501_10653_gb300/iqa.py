@@ -1,0 +1,209 @@
+"""Thin ctypes binding of ``libiqa.so`` (declared in ``include/iqa.h``).
+
+Argument marshalling only: every step of the map computation runs in the
+library's CUDA kernels.  Functions keep the C names.  Pointer arguments accept
+an int address or any object with ``data_ptr()`` (a torch tensor); stream
+arguments accept an int handle, ``None`` (legacy default stream) or an object
+with a ``cuda_stream`` attribute (``torch.cuda.Stream``).  A non-OK status
+raises ``IqaError`` carrying the status and ``iqa_last_error``.
+
+The library must have been built (``paper_2501_10653_gb300.build.build()``);
+there is no fallback: loading fails loudly if it is missing.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libiqa.so")
+
+IQA_OK = 0
+IQA_PENDING = 1
+IQA_ERR_INVALID_ARG = -1
+IQA_ERR_NOMEM = -2
+IQA_ERR_CUDA = -3
+IQA_ERR_TIMEOUT = -4
+IQA_ERR_BUSY = -5
+IQA_ERR_UNSUPPORTED = -6
+
+IQA_F32 = 0
+IQA_F16 = 1
+IQA_BF16 = 2
+
+MAPS_LISI = 1
+MAPS_AUGLISI = 2
+MAPS_BOTH = 3
+
+STATUS_NAMES = {
+    0: "IQA_OK", 1: "IQA_PENDING", -1: "IQA_ERR_INVALID_ARG", -2: "IQA_ERR_NOMEM",
+    -3: "IQA_ERR_CUDA", -4: "IQA_ERR_TIMEOUT", -5: "IQA_ERR_BUSY",
+    -6: "IQA_ERR_UNSUPPORTED",
+}
+
+
+class IqaError(RuntimeError):
+    def __init__(self, status, message):
+        self.status = status
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+
+
+class iqa_params(ctypes.Structure):
+    _fields_ = [("C1", ctypes.c_double), ("C2", ctypes.c_double),
+                ("C", ctypes.c_double), ("D", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"C1": self.C1, "C2": self.C2, "C": self.C, "D": self.D}
+
+
+class iqa_launch_config(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int), ("ilp", ctypes.c_int),
+                ("tiles_across", ctypes.c_int), ("split", ctypes.c_int),
+                ("vector", ctypes.c_int), ("variant", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_sz = ctypes.c_size_t
+_st = ctypes.c_int
+
+
+def _declare(lib):
+    P = ctypes.POINTER
+    sig = {
+        "iqa_version": ([], ctypes.c_char_p),
+        "iqa_default_params": ([P(iqa_params)], _st),
+        "iqa_create": ([P(_vp), _i, _sz], _st),
+        "iqa_destroy": ([_vp], None),
+        "iqa_last_error": ([_vp], ctypes.c_char_p),
+        "iqa_lisi": ([_vp, _vp, _vp, _i, _i, _i, P(iqa_params), _vp, _vp, _vp], _st),
+        "iqa_auglisi": ([_vp, _vp, _vp, _i, _i, _i, P(iqa_params), _vp, _vp, _vp], _st),
+        "iqa_both": ([_vp, _vp, _vp, _i, _i, _i, P(iqa_params), _vp, _vp, _vp, _vp], _st),
+        "iqa_both_host": ([_vp, _vp, _vp, _i, _i, _i, P(iqa_params), _vp, _vp, _vp], _st),
+        "iqa_get_config": ([_vp, _i, _i, _i, _i, P(iqa_launch_config)], _st),
+        "iqa_set_config": ([_vp, _i, _i, _i, _i, P(iqa_launch_config)], _st),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                "libiqa.so is not built (expected at %s); run "
+                "paper_2501_10653_gb300.build.build() -- there is no CPU fallback"
+                % LIB_PATH)
+        _lib = _declare(ctypes.CDLL(LIB_PATH))
+    return _lib
+
+
+def _ptr(p):
+    if p is None:
+        return None
+    if isinstance(p, int):
+        return p
+    if hasattr(p, "data_ptr"):
+        return p.data_ptr()
+    if hasattr(p, "ctypes"):  # numpy array (host path)
+        return p.ctypes.data
+    raise TypeError("expected an address, a tensor or an array, got %r" % type(p))
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(ctx, status):
+    if status != IQA_OK:
+        msg = lib().iqa_last_error(ctx)
+        raise IqaError(status, msg.decode() if msg else "")
+    return status
+
+
+def _params(p):
+    if p is None:
+        return None
+    if isinstance(p, iqa_params):
+        return ctypes.byref(p)
+    if isinstance(p, dict):
+        return ctypes.byref(iqa_params(p.get("C1", 1e-6), p.get("C2", 1e-6),
+                                       p.get("C", 1e-6), p.get("D", 0.0)))
+    raise TypeError("params must be iqa_params, a dict or None")
+
+
+def iqa_version():
+    return lib().iqa_version().decode()
+
+
+def iqa_default_params():
+    p = iqa_params()
+    _check(None, lib().iqa_default_params(ctypes.byref(p)))
+    return p
+
+
+def iqa_create(device=0, hbm_budget_bytes=0):
+    h = _vp()
+    _check(None, lib().iqa_create(ctypes.byref(h), int(device), int(hbm_budget_bytes)))
+    return h.value
+
+
+def iqa_destroy(ctx):
+    lib().iqa_destroy(ctx)
+
+
+def iqa_last_error(ctx):
+    m = lib().iqa_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def iqa_lisi(ctx, x, y, dtype, N, NT, params, map, sums=None, stream=None):
+    return _check(ctx, lib().iqa_lisi(ctx, _ptr(x), _ptr(y), dtype, N, NT,
+                                      _params(params), _ptr(map), _ptr(sums),
+                                      _stream(stream)))
+
+
+def iqa_auglisi(ctx, x, y, dtype, N, NT, params, map, sums=None, stream=None):
+    return _check(ctx, lib().iqa_auglisi(ctx, _ptr(x), _ptr(y), dtype, N, NT,
+                                         _params(params), _ptr(map), _ptr(sums),
+                                         _stream(stream)))
+
+
+def iqa_both(ctx, x, y, dtype, N, NT, params, lisi_map, aug_map, sums=None,
+             stream=None):
+    return _check(ctx, lib().iqa_both(ctx, _ptr(x), _ptr(y), dtype, N, NT,
+                                      _params(params), _ptr(lisi_map),
+                                      _ptr(aug_map), _ptr(sums), _stream(stream)))
+
+
+def iqa_both_host(ctx, hx, hy, dtype, N, NT, params, lisi_map, aug_map, sums=None):
+    return _check(ctx, lib().iqa_both_host(ctx, _ptr(hx), _ptr(hy), dtype, N, NT,
+                                           _params(params), _ptr(lisi_map),
+                                           _ptr(aug_map), _ptr(sums)))
+
+
+def iqa_get_config(ctx, dtype, N, NT, maps):
+    c = iqa_launch_config()
+    _check(ctx, lib().iqa_get_config(ctx, dtype, N, NT, maps, ctypes.byref(c)))
+    return c
+
+
+def iqa_set_config(ctx, dtype, N, NT, maps, cfg):
+    if cfg is None:
+        ref = None
+    else:
+        if isinstance(cfg, dict):
+            cfg = iqa_launch_config(**cfg)
+        ref = ctypes.byref(cfg)
+    return _check(ctx, lib().iqa_set_config(ctx, dtype, N, NT, maps, ref))

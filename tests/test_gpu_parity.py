@@ -1,0 +1,264 @@
+"""CUDA path against the FP64 oracle, through the C-ABI (needs a GPU).
+
+Inputs are the seeded synthetic skies of ``paper_2501_10653_gb300.synth``;
+every comparison is element by element on all tiles (or, at full size, on
+sampled tiles the oracle computes one by one), with the tolerance stated in
+``tests/parity.py``.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import parity
+from paper_2501_10653_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+PARAMS = {"C1": 1e-6, "C2": 1e-6, "C": 1e-6, "D": 0.0}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_2501_10653_gb300 import build, iqa
+    build.build()
+    assert torch.cuda.is_available()
+    h = iqa.iqa_create(0, 0)
+    yield h
+    iqa.iqa_destroy(h)
+
+
+@pytest.fixture(scope="module")
+def small():
+    return synth.small_pair()
+
+
+@pytest.fixture(scope="module")
+def paper():
+    return synth.paper_pair()
+
+
+def test_small_pair_all_outputs(ctx, orc, small):
+    x, y = small
+    want = parity.oracle_maps(orc, x, y, 64, PARAMS)
+    for which in ("both", "lisi", "aug", "both_nosums"):
+        got = parity.gpu_maps(ctx, x, y, 64, PARAMS, which)
+        parity.assert_parity(got, want, PARAMS)
+
+
+@pytest.mark.parametrize("NT", synth.PAPER_NT_SWEEP)
+def test_paper_pair_nt_sweep(ctx, orc, paper, NT):
+    x, y = paper
+    want = parity.oracle_maps(orc, x, y, NT, PARAMS)
+    got = parity.gpu_maps(ctx, x, y, NT, PARAMS)
+    parity.assert_parity(got, want, PARAMS)
+
+
+def _all_configs(N, NT):
+    T = N // NT
+    for threads, ilp, vector in itertools.product((128, 256, 512), (2, 4, 8), (1, 0)):
+        if vector == 0 and (threads, ilp) != (256, 8):
+            continue
+        for TX in [d for d in range(1, min(T, 64) + 1) if T % d == 0]:
+            for S in [s for s in range(1, 9) if NT % s == 0]:
+                yield dict(threads=threads, ilp=ilp, tiles_across=TX, split=S,
+                           vector=vector, variant=0)
+
+
+@pytest.mark.parametrize("N,NT", [(512, 16), (512, 64), (512, 256), (480, 48),
+                                  (384, 128), (512, 512)])
+def test_every_launch_shape(ctx, orc, N, NT):
+    """Every valid launch shape gives oracle parity (several tiles per unit,
+    clusters of 2..8 CTAs per tile, ragged per-thread item counts)."""
+    from paper_2501_10653_gb300 import iqa
+    x, y = synth.paper_pair(N=N)
+    want = parity.oracle_maps(orc, x, y, NT, PARAMS)
+    dx, dy = parity.to_device(x), parity.to_device(y)
+    n_ok = 0
+    for cfg in _all_configs(N, NT):
+        try:
+            iqa.iqa_set_config(ctx, iqa.IQA_F32, N, NT, iqa.MAPS_BOTH, cfg)
+        except iqa.IqaError as e:
+            assert e.status == iqa.IQA_ERR_INVALID_ARG
+            continue
+        got = parity.gpu_maps(ctx, x, y, NT, PARAMS, dx=dx, dy=dy)
+        parity.assert_parity(got, want, PARAMS)
+        n_ok += 1
+    iqa.iqa_set_config(ctx, iqa.IQA_F32, N, NT, iqa.MAPS_BOTH, None)
+    assert n_ok >= 3
+
+
+@pytest.mark.parametrize("N,NT", [(100, 10), (96, 12), (200, 40), (66, 33), (8, 8)])
+def test_odd_shapes_scalar_and_vector(ctx, orc, N, NT):
+    """Tiles that are not whole 16-byte vectors take the scalar path."""
+    x, y = synth.paper_pair(N=N)
+    want = parity.oracle_maps(orc, x, y, NT, PARAMS)
+    parity.assert_parity(parity.gpu_maps(ctx, x, y, NT, PARAMS), want, PARAMS)
+
+
+def test_misaligned_pointers_use_scalar_path(ctx, orc):
+    import torch
+    N, NT = 256, 32
+    x, y = synth.paper_pair(N=N)
+    want = parity.oracle_maps(orc, x, y, NT, PARAMS)
+    bx = torch.zeros(N * N + 1, dtype=torch.float32, device="cuda")
+    by = torch.zeros(N * N + 3, dtype=torch.float32, device="cuda")
+    bx[1:].copy_(torch.from_numpy(x.ravel()))
+    by[3:].copy_(torch.from_numpy(y.ravel()))
+    got = parity.gpu_maps(ctx, x, y, NT, PARAMS, dx=bx[1:], dy=by[3:])
+    parity.assert_parity(got, want, PARAMS)
+
+
+@pytest.mark.parametrize("dt", ["f16", "bf16"])
+@pytest.mark.parametrize("NT", [16, 64, 256])
+def test_16bit_storage_against_oracle_on_rounded_inputs(ctx, orc, dt, NT):
+    x, y = synth.paper_pair(N=1024, dtype=dt)
+    want = parity.oracle_maps(orc, x, y, NT, PARAMS)
+    parity.assert_parity(parity.gpu_maps(ctx, x, y, NT, PARAMS), want, PARAMS)
+
+
+def test_other_constants(ctx, orc, paper):
+    x, y = paper
+    p = {"C1": 1e-3, "C2": 0.5, "C": 0.25, "D": 0.125}
+    want = parity.oracle_maps(orc, x, y, 64, p)
+    parity.assert_parity(parity.gpu_maps(ctx, x, y, 64, p), want, p)
+
+
+def test_all_zero_and_negative_tiles_exact(ctx):
+    """Clamped-to-zero tiles: LISI exactly 0, augLISI exactly 1."""
+    N = 256
+    x = -np.abs(np.random.default_rng(1).standard_normal((N, N))).astype(np.float32)
+    y = np.zeros((N, N), np.float32)
+    y[::3, ::5] = np.nan
+    l, a, s = parity.gpu_maps(ctx, x, y, 32, PARAMS)
+    assert np.all(l == 0.0) and np.all(a == 1.0) and np.all(s == 0.0)
+
+
+def test_identical_inputs(ctx, orc, paper):
+    """x = y: augLISI exactly 1, LISI = Sx/(Sx + C2) within tolerance."""
+    x, _ = paper
+    l, a, s = parity.gpu_maps(ctx, x, x, 64, PARAMS)
+    assert np.all(a == 1.0)
+    _, _, osum = parity.oracle_maps(orc, x, x, 64, PARAMS)
+    sx = osum[:, 2]
+    parity.assert_lisi_close(l, sx / (sx + PARAMS["C2"]))
+
+
+def test_nan_pixels_read_as_zero(ctx, orc, paper):
+    x, y = paper
+    x = x.copy()
+    y = y.copy()
+    rng = np.random.default_rng(5)
+    x[rng.random(x.shape) < 0.01] = np.nan
+    y[rng.random(y.shape) < 0.01] = np.nan
+    want = parity.oracle_maps(orc, x, y, 64, PARAMS)
+    parity.assert_parity(parity.gpu_maps(ctx, x, y, 64, PARAMS), want, PARAMS)
+
+
+def test_tile_markers_bit_exact_indexing(ctx):
+    """Changing one tile of y changes exactly its own entry of each map."""
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    N, NT = 512, 64
+    T = N // NT
+    x, y = synth.paper_pair(N=N)
+    base_l, base_a, _ = parity.gpu_maps(ctx, x, y, NT, PARAMS, "both_nosums")
+    for r in range(T):
+        for c in range(T):
+            y2 = y.copy()
+            y2[r * NT + 5, c * NT + 7] += 0.5
+            l, a, _ = parity.gpu_maps(ctx, x, y2, NT, PARAMS, "both_nosums")
+            dl = np.argwhere(l.ravel() != base_l.ravel()).ravel().tolist()
+            da = np.argwhere(a.ravel() != base_a.ravel()).ravel().tolist()
+            assert dl == [r * T + c] and da == [r * T + c], (r, c, dl, da)
+
+
+def test_inputs_not_written_and_deterministic(ctx, paper):
+    import torch
+    x, y = paper
+    dx, dy = parity.to_device(x), parity.to_device(y)
+    r1 = parity.gpu_maps(ctx, x, y, 64, PARAMS, dx=dx, dy=dy)
+    r2 = parity.gpu_maps(ctx, x, y, 64, PARAMS, dx=dx, dy=dy)
+    for u, v in zip(r1, r2):
+        assert np.array_equal(u, v)
+    assert np.array_equal(dx.cpu().numpy(), x)
+    assert np.array_equal(dy.cpu().numpy(), y)
+
+
+def test_host_path_matches_device_path_bitwise(ctx, paper):
+    from paper_2501_10653_gb300 import iqa
+    import torch
+    x, y = paper
+    N, NT = 2048, 64
+    T = N // NT
+    dev = parity.gpu_maps(ctx, x, y, NT, PARAMS)
+    hx = torch.from_numpy(x).pin_memory()
+    hy = torch.from_numpy(y).pin_memory()
+    l = np.full((T, T), np.nan, np.float32)
+    a = np.full((T, T), np.nan, np.float32)
+    s = np.full((T * T, 4), np.nan, np.float64)
+    iqa.iqa_both_host(ctx, hx, hy, iqa.IQA_F32, N, NT, PARAMS, l, a, s)
+    assert np.array_equal(l, dev[0]) and np.array_equal(a, dev[1])
+    assert np.array_equal(s, dev[2])
+    # pageable host memory works too
+    l2 = np.zeros_like(l)
+    iqa.iqa_both_host(ctx, x, y, iqa.IQA_F32, N, NT, PARAMS, l2, None, None)
+    assert np.array_equal(l2, dev[0])
+
+
+def test_full_size_sampled_tiles(ctx, orc):
+    """N = 8192, N_T = 64 (the precision workload's size), FP32: sampled tiles
+    against the oracle computed tile by tile."""
+    x, y = synth.precision_pair(0)
+    N, NT = 8192, 64
+    T = N // NT
+    got = parity.gpu_maps(ctx, x, y, NT, PARAMS)
+    rng = np.random.default_rng(9)
+    pick = np.unique(np.concatenate([rng.integers(0, T * T, 200),
+                                     [0, T - 1, T * T - T, T * T - 1]]))
+    osums = orc.tile_sums(x, y, NT, PARAMS["C1"], tiles=pick)
+    A, B, Sx, Sy = osums.T
+    D = PARAMS["C1"] / 2
+    ol = D * A / (np.maximum(Sx, Sy) + PARAMS["C2"])
+    oa = 1 - B / (Sx + Sy + PARAMS["C"])
+    r = B / (Sx + Sy + PARAMS["C"])
+    parity.assert_lisi_close(got[0].ravel()[pick], ol)
+    parity.assert_aug_close(got[1].ravel()[pick], oa, r)
+    parity.assert_sums_close(got[2][pick], osums)
+
+
+def test_whole_image_as_one_tile(ctx, orc, paper):
+    """N_T = N: one tile over the whole 2048^2 image (a cluster of CTAs)."""
+    x, y = paper
+    want = parity.oracle_maps(orc, x, y, 2048, PARAMS)
+    parity.assert_parity(parity.gpu_maps(ctx, x, y, 2048, PARAMS), want, PARAMS)
+
+
+def test_bad_arguments_rejected(ctx):
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    d = torch.zeros(64 * 64, device="cuda")
+    m = torch.zeros(16, device="cuda")
+    cases = [
+        dict(x=None, y=d, N=64, NT=16, m=m),
+        dict(x=d, y=d, N=64, NT=12, m=m),
+        dict(x=d, y=d, N=0, NT=16, m=m),
+        dict(x=d, y=d, N=64, NT=0, m=m),
+        dict(x=d, y=d, N=64, NT=128, m=m),
+    ]
+    for c in cases:
+        with pytest.raises(iqa.IqaError) as ei:
+            iqa.iqa_both(ctx, c["x"], c["y"], iqa.IQA_F32, c["N"], c["NT"], None,
+                         c["m"], None)
+        assert ei.value.status == iqa.IQA_ERR_INVALID_ARG
+    with pytest.raises(iqa.IqaError) as ei:
+        iqa.iqa_both(ctx, d, d, iqa.IQA_F32, 64, 16, {"C1": 0.0}, m, None)
+    assert ei.value.status == iqa.IQA_ERR_INVALID_ARG
+    with pytest.raises(iqa.IqaError) as ei:
+        iqa.iqa_both(ctx, d, d, 7, 64, 16, None, m, None)
+    assert ei.value.status == iqa.IQA_ERR_INVALID_ARG
+    with pytest.raises(iqa.IqaError) as ei:
+        iqa.iqa_both(ctx, d, d, iqa.IQA_F32, 64, 16, None, None, None)
+    assert ei.value.status == iqa.IQA_ERR_INVALID_ARG
+    torch.cuda.synchronize()
