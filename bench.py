@@ -273,12 +273,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(K // G):
-        graph.replay()
-    if graph_tail is not None:
-        graph_tail.replay()
-    e1.record(stream)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(K // G):
+            graph.replay()
+        if graph_tail is not None:
+            graph_tail.replay()
+        e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
     dev_ms = e0.elapsed_time(e1)

@@ -151,11 +151,13 @@ iqa_status iqa_both_host(iqa_ctx *ctx, const void *hx, const void *hy,
                          float *aug_map, double *sums);
 
 /*
- * Launch shape of the tile kernel for one (dtype, N, NT, maps) key.  The paper
- * gives each tile one thread block (Section 2); here a CTA streams a "unit" of
+ * Launch shape for one (dtype, N, NT, maps) key.  The paper gives each tile
+ * one thread block (Section 2).  Two kernels are built:
+ *
+ * variant 0, the streaming-load kernel: a CTA streams a "unit" of
  * `tiles_across` whole tiles side by side, or 1/`split` of one tile's rows,
- * with the `split` CTAs of a tile forming a thread-block cluster that combines
- * its partial sums in distributed shared memory.
+ * with 16-byte non-caching loads; the `split` CTAs of a tile form a thread-
+ * block cluster that combines its partial sums in distributed shared memory.
  *   threads        128, 256 or 512 threads per CTA
  *   ilp            2, 4 or 8: 16-byte loads of each image in flight per thread
  *   tiles_across   whole tiles per CTA (divides N/NT, <= 64)
@@ -163,17 +165,28 @@ iqa_status iqa_both_host(iqa_ctx *ctx, const void *hx, const void *hy,
  *                  tiles_across == 1
  *   vector         1: 16-byte loads (needs 16-byte aligned images and NT a
  *                  multiple of 16 bytes); 0: scalar loads, 256 threads, ilp 8
- *   variant        0: the streaming-load kernel
+ *
+ * variant 1, the persistent TMA kernel: `ctas_per_sm` CTAs per SM loop over
+ * units of `tiles_across` whole tiles; a producer warp streams each unit in
+ * chunks with 2-D tensor copies into a ring of `stages` shared-memory stages of
+ * `stage_kb` KB per image, and `threads` consumer threads reduce them.  Needs
+ * 16-byte aligned images, NT a multiple of 16 bytes, tiles_across * NT <= 256.
+ *   threads        128, 256 or 512 consumer threads (plus one producer warp)
+ *   tiles_across   whole tiles per unit
+ *   stages         2..16;   stage_kb  2, 4, 8 or 16;   ctas_per_sm  1 or 2
  * maps: 1 = LISI only, 2 = augLISI only, 3 = both (also used when sums are
- * requested).
+ * requested).  Unused fields are ignored.
  */
 typedef struct {
+    int variant;
     int threads;
     int ilp;
     int tiles_across;
     int split;
     int vector;
-    int variant;
+    int stages;
+    int stage_kb;
+    int ctas_per_sm;
 } iqa_launch_config;
 
 /*
@@ -188,10 +201,111 @@ iqa_status iqa_get_config(iqa_ctx *ctx, iqa_dtype dtype, int N, int NT, int maps
  * Pins a launch shape for this key (cfg == NULL removes the pin).  Results do
  * not depend on the shape beyond FP32 summation order.
  * Errors: IQA_ERR_INVALID_ARG (shape not valid for this key; reason in
- * iqa_last_error), IQA_ERR_UNSUPPORTED (variant not built).
+ * iqa_last_error), IQA_ERR_UNSUPPORTED (unknown variant).
  */
 iqa_status iqa_set_config(iqa_ctx *ctx, iqa_dtype dtype, int N, int NT, int maps,
                           const iqa_launch_config *cfg);
+
+/* ---------------------------------------------------------------------------
+ * Batched form: many pairs, one persistent launch.
+ *
+ * A plan fixes a list of image pairs (any mix of N and N_T, one storage dtype,
+ * one set of constants) and their outputs.  One launch of the persistent
+ * TMA-pipelined kernel then computes every pair's maps: its CTAs take units of
+ * whole tiles of all pairs from one work list in device memory (largest units
+ * first, handed out by a device-side counter), so small images no longer pay
+ * a launch and a ramp-up each.  Results of a pair do not depend on the other
+ * pairs of the plan (each tile's summation order depends only on the pair's
+ * own N, N_T and the plan's launch shape).
+ */
+typedef struct {
+    const void *x;         /* device pointer, N*N elements, 16-byte aligned  */
+    const void *y;         /* device pointer, N*N elements, 16-byte aligned  */
+    int N;                 /* image side                                      */
+    int NT;                /* tile side: divides N, a multiple of 16 bytes,
+                              at most 256                                     */
+    float *lisi_map;       /* device (N/NT)^2 float32, or NULL                */
+    float *aug_map;        /* device (N/NT)^2 float32, or NULL                */
+    double *sums;          /* device (N/NT)^2 x 4 float64, or NULL            */
+} iqa_pair;
+
+typedef struct iqa_plan iqa_plan;
+
+/* iqa_plan_create flag: capture the launch as a CUDA graph, replayed by
+ * iqa_plan_launch. */
+#define IQA_PLAN_GRAPH 1
+
+/*
+ * Builds a plan over `npairs` pairs: validates them, encodes one TMA tensor
+ * map per image, uploads the work-list descriptors to device memory owned by
+ * the plan, and (with IQA_PLAN_GRAPH) captures the launch in a CUDA graph.
+ * The pair array is copied; the buffers it points to must stay valid while
+ * the plan is used.  Synchronous.
+ * Errors: IQA_ERR_INVALID_ARG (bad pair, shape, dtype, constants),
+ * IQA_ERR_UNSUPPORTED (a pair the TMA kernel cannot stream: unaligned images,
+ * NT not a multiple of 16 bytes or above 256), IQA_ERR_NOMEM, IQA_ERR_CUDA.
+ */
+iqa_status iqa_plan_create(iqa_ctx *ctx, const iqa_pair *pairs, int npairs,
+                           iqa_dtype dtype, const iqa_params *params, int flags,
+                           iqa_plan **out);
+
+/*
+ * Enqueues the plan's launch (graph replay, or a direct launch) on `stream`.
+ * Stream-ordered, returns without synchronising.  Launches of the same plan
+ * must not overlap in time (they share the plan's work counter): issue them
+ * on one stream, or order them with events.
+ */
+iqa_status iqa_plan_launch(iqa_plan *plan, iqa_stream stream);
+
+/* Frees the plan (its graph, descriptors and counter).  The caller must make
+ * sure no launch of the plan is still running.  NULL is ignored. */
+void iqa_plan_destroy(iqa_plan *plan);
+
+typedef struct {
+    int npairs;
+    long long total_units;          /* work-list length                  */
+    int grid;                       /* persistent CTAs per launch        */
+    unsigned long long input_bytes; /* algorithmic bytes read per launch */
+    int graph;                      /* 1 if launches replay a CUDA graph */
+    iqa_launch_config config;       /* variant 1 shape in use            */
+} iqa_plan_stats;
+
+iqa_status iqa_plan_info(const iqa_plan *plan, iqa_plan_stats *out);
+
+/*
+ * Autotuner: times the plan under several launch shapes of the persistent
+ * kernel (consumer threads, ring depth, stage size, CTAs per SM), `iters`
+ * launches each on `stream` (synchronising it), keeps the fastest, re-captures
+ * the graph, and remembers the shape for later plans of the same dtype on
+ * this context.  *best_out (nullable) receives it.
+ */
+iqa_status iqa_plan_autotune(iqa_plan *plan, iqa_stream stream, int iters,
+                             iqa_launch_config *best_out);
+
+/*
+ * Waits, at most timeout_us microseconds (< 0: no limit), for `stream` to
+ * drain, then reads the context's device status word, which the persistent
+ * kernels set when one of their bounded device-side waits runs out.
+ * Returns IQA_OK, IQA_ERR_TIMEOUT (stream still busy, or a device-side wait
+ * ran out; the status word is then cleared) or IQA_ERR_CUDA.
+ */
+iqa_status iqa_wait(iqa_ctx *ctx, iqa_stream stream, int timeout_us);
+
+/* Context options for iqa_set_option. */
+typedef enum {
+    /* Bound, in microseconds, on every device-side wait of the persistent
+     * kernels (default 1000000).  A wait that runs out makes the kernel record
+     * an error in the status word, stop, and return (see iqa_wait). */
+    IQA_OPT_WAIT_TIMEOUT_US = 1,
+    /* Fault injection for tests of the failure path: 1 makes the producer warp
+     * of the persistent kernels issue no copies, so every consumer wait runs
+     * out; 0 (default) is normal operation. */
+    IQA_OPT_INJECT_STALL = 2
+} iqa_option;
+
+/* Sets a context option.  Errors: IQA_ERR_INVALID_ARG (unknown option or
+ * value out of range: the timeout must be 1 us .. 60 s). */
+iqa_status iqa_set_option(iqa_ctx *ctx, int option, long long value);
 
 #ifdef __cplusplus
 }

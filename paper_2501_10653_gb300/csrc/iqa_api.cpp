@@ -2,6 +2,7 @@
 // shapes, and the plain (one pair per call) LISI / augLISI map path.
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -10,6 +11,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -122,6 +124,15 @@ bool config_valid(int N, int NT, iqa_dtype dtype, const TileConfig &c,
     return true;
 }
 
+bool any_config_valid(int N, int NT, iqa_dtype dtype, const TileConfig &c,
+                      std::string *why)
+{
+    if (c.variant == 0) return config_valid(N, NT, dtype, c, why);
+    if (c.variant == 1) return stream_config_valid(N, NT, dtype, c, why);
+    if (why) *why = "unknown variant";
+    return false;
+}
+
 // Launch shape when nothing was tuned (measured on GB300: 128-thread CTAs
 // with 8 loads of each image in flight per thread, and units of up to 16K
 // pixel pairs, stream best).  Units shrink for small images so that there are
@@ -182,7 +193,7 @@ TileConfig pick_config(iqa_ctx *ctx, int N, int NT, iqa_dtype dtype, int maps,
         auto it = ctx->pinned.find(std::make_tuple((int)dtype, N, NT, maps));
         if (it != ctx->pinned.end()) {
             const TileConfig &c = it->second;
-            if (c.vec == 1 || aligned) return c;
+            if ((c.variant == 0 && c.vec == 1) || aligned) return c;
         }
     }
     return default_config(N, NT, dtype, aligned, ctx->num_sms);
@@ -254,10 +265,13 @@ static iqa_status run_maps(iqa_ctx *ctx, const void *x, const void *y,
     const bool aligned = aligned16(x) && aligned16(y);
     TileConfig c = pick_config(ctx, N, NT, dtype, maps, aligned);
     std::string why;
-    if (!config_valid(N, NT, dtype, c, &why)) {
+    if (!any_config_valid(N, NT, dtype, c, &why)) {
         set_error(ctx, "no launch shape for N=%d NT=%d: %s", N, NT, why.c_str());
         return IQA_ERR_UNSUPPORTED;
     }
+    if (c.variant == 1)
+        return run_stream_pair(ctx, x, y, dtype, N, NT, c, P, lisi, aug, sums, maps,
+                               (cudaStream_t)stream);
     TileArgs a = make_args(x, y, N, NT, c, P, lisi, aug, sums);
     cudaError_t e = launch_tiles(a, c, dtype, maps, N / NT, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tile kernel launch");
@@ -307,10 +321,12 @@ iqa_status iqa_create(iqa_ctx **out, int device, size_t hbm_budget_bytes)
     cudaDeviceGetAttribute(&ctx->cc_minor, cudaDevAttrComputeCapabilityMinor, device);
     e = cudaStreamCreateWithFlags(&ctx->s_copy, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->s_comp, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, 256);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, 256);
     cudaSetDevice(prev);
     if (e != cudaSuccess) {
         iqa_destroy(ctx);
-        return cuda_fail(nullptr, e, "cudaStreamCreate");
+        return cuda_fail(nullptr, e, "context set-up");
     }
     *out = ctx;
     return IQA_OK;
@@ -326,6 +342,7 @@ void iqa_destroy(iqa_ctx *ctx)
     if (ctx->s_comp) cudaStreamSynchronize(ctx->s_comp);
     for (cudaEvent_t ev : ctx->band_events) cudaEventDestroy(ev);
     if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->s_copy) cudaStreamDestroy(ctx->s_copy);
     if (ctx->s_comp) cudaStreamDestroy(ctx->s_comp);
     cudaSetDevice(prev);
@@ -379,13 +396,35 @@ iqa_status iqa_get_config(iqa_ctx *ctx, iqa_dtype dtype, int N, int NT, int maps
     iqa_status s = check_shape(ctx, N, NT);
     if (s != IQA_OK) return s;
     TileConfig c = pick_config(ctx, N, NT, dtype, maps, true);
+    out->variant = c.variant;
     out->threads = c.threads;
     out->ilp = c.ilp;
     out->tiles_across = c.TX;
     out->split = c.S;
     out->vector = c.vec == 1 ? 0 : 1;
-    out->variant = 0;
+    out->stages = c.stages;
+    out->stage_kb = c.stage_kb;
+    out->ctas_per_sm = c.ctas_per_sm;
     return IQA_OK;
+}
+
+TileConfig from_public(const iqa_launch_config *cfg, iqa_dtype dtype)
+{
+    TileConfig c;
+    c.variant = cfg->variant;
+    c.threads = cfg->threads;
+    c.ilp = cfg->ilp;
+    c.TX = cfg->tiles_across;
+    c.S = cfg->split;
+    c.vec = cfg->vector ? 16 / elem_size(dtype) : 1;
+    c.stages = cfg->stages;
+    c.stage_kb = cfg->stage_kb;
+    c.ctas_per_sm = cfg->ctas_per_sm;
+    if (c.variant == 1) {
+        c.S = 1;
+        c.vec = 16 / elem_size(dtype);
+    }
+    return c;
 }
 
 iqa_status iqa_set_config(iqa_ctx *ctx, iqa_dtype dtype, int N, int NT, int maps,
@@ -404,23 +443,70 @@ iqa_status iqa_set_config(iqa_ctx *ctx, iqa_dtype dtype, int N, int NT, int maps
         ctx->pinned.erase(key);
         return IQA_OK;
     }
-    TileConfig c;
-    c.threads = cfg->threads;
-    c.ilp = cfg->ilp;
-    c.TX = cfg->tiles_across;
-    c.S = cfg->split;
-    c.vec = cfg->vector ? 16 / elem_size(dtype) : 1;
-    if (cfg->variant != 0) {
-        set_error(ctx, "variant %d is not built", cfg->variant);
+    if (cfg->variant != 0 && cfg->variant != 1) {
+        set_error(ctx, "unknown variant %d", cfg->variant);
         return IQA_ERR_UNSUPPORTED;
     }
+    TileConfig c = from_public(cfg, dtype);
     std::string why;
-    if (!config_valid(N, NT, dtype, c, &why)) {
+    if (!any_config_valid(N, NT, dtype, c, &why)) {
         set_error(ctx, "invalid launch config: %s", why.c_str());
         return IQA_ERR_INVALID_ARG;
     }
     std::lock_guard<std::mutex> g(ctx->cfg_mu);
     ctx->pinned[key] = c;
+    return IQA_OK;
+}
+
+iqa_status iqa_set_option(iqa_ctx *ctx, int option, long long value)
+{
+    if (!ctx) return IQA_ERR_INVALID_ARG;
+    switch (option) {
+    case IQA_OPT_WAIT_TIMEOUT_US:
+        if (value < 1 || value > 60000000LL) {
+            set_error(ctx, "wait timeout must be 1 us .. 60 s");
+            return IQA_ERR_INVALID_ARG;
+        }
+        ctx->wait_timeout_ns = value * 1000LL;
+        return IQA_OK;
+    case IQA_OPT_INJECT_STALL:
+        if (value != 0 && value != 1) {
+            set_error(ctx, "inject-stall takes 0 or 1");
+            return IQA_ERR_INVALID_ARG;
+        }
+        ctx->inject_stall = (int)value;
+        return IQA_OK;
+    default:
+        set_error(ctx, "unknown option %d", option);
+        return IQA_ERR_INVALID_ARG;
+    }
+}
+
+iqa_status iqa_wait(iqa_ctx *ctx, iqa_stream stream, int timeout_us)
+{
+    if (!ctx) return IQA_ERR_INVALID_ARG;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery((cudaStream_t)stream);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(ctx, e, "stream");
+        auto us = std::chrono::duration_cast<std::chrono::microseconds>(
+                      std::chrono::steady_clock::now() - t0)
+                      .count();
+        if (timeout_us >= 0 && us > timeout_us) {
+            set_error(ctx, "stream still busy after %d us", timeout_us);
+            return IQA_ERR_TIMEOUT;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    int code = 0;
+    cudaError_t e = cudaMemcpy(&code, ctx->d_status, sizeof code, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status read");
+    if (code != 0) {
+        cudaMemset(ctx->d_status, 0, sizeof code);
+        set_error(ctx, "a device-side wait ran out of time (code %d)", code);
+        return IQA_ERR_TIMEOUT;
+    }
     return IQA_OK;
 }
 

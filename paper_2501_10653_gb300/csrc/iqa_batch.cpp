@@ -1,0 +1,359 @@
+// iqa_batch.cpp -- batched form: many image pairs (any mix of N and N_T) in
+// ONE persistent launch of iqa_stream_kernel over a (pair, unit) work list,
+// optionally captured as a CUDA graph, with a per-plan autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "iqa.h"
+#include "iqa_ctx.h"
+#include "iqa_stream.cuh"
+
+using namespace iqa;
+
+struct iqa_plan {
+    iqa_ctx *ctx = nullptr;
+    iqa_dtype dtype = IQA_F32;
+    iqa_params P{};
+    TileConfig cfg;          // shared by all pairs (TX is chosen per pair)
+    int maps = MAPS_AB;
+    std::vector<iqa_pair> pairs;  // in work-list order (largest units first)
+    PairDesc *h_table = nullptr;  // 128-byte aligned host copy
+    PairDesc *d_table = nullptr;
+    unsigned long long *d_sched = nullptr;
+    long long total_units = 0;
+    int grid = 0;
+    size_t table_bytes = 0;
+    unsigned long long input_bytes = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int flags = 0;
+};
+
+namespace iqa {
+
+// Widest unit (whole tiles, <= 256 elements, <= 16K pixels) whose row of
+// 16-byte vectors divides the consumer thread count.
+static int batch_tiles_across(int N, int NT, iqa_dtype dtype, int threads)
+{
+    const int V = 16 / elem_size(dtype);
+    const int T = N / NT;
+    int best = 1;
+    for (int tx = 2; tx <= kMaxTX && tx * NT <= 256; ++tx) {
+        if (T % tx) continue;
+        if ((long long)tx * NT * NT > 16384) break;
+        if (threads % (tx * NT / V)) continue;
+        best = tx;
+    }
+    return best;
+}
+
+static iqa_status check_pair(iqa_ctx *ctx, const iqa_pair &p, iqa_dtype dtype, int i)
+{
+    if (!p.x || !p.y) {
+        set_error(ctx, "pair %d: x and y must be device pointers", i);
+        return IQA_ERR_INVALID_ARG;
+    }
+    if (!p.lisi_map && !p.aug_map && !p.sums) {
+        set_error(ctx, "pair %d: no output requested", i);
+        return IQA_ERR_INVALID_ARG;
+    }
+    iqa_status s = check_shape(ctx, p.N, p.NT);
+    if (s != IQA_OK) return s;
+    const int V = 16 / elem_size(dtype);
+    if (((uintptr_t)p.x & 15u) || ((uintptr_t)p.y & 15u) || p.NT % V || p.NT > 256) {
+        set_error(ctx, "pair %d: the batched kernel needs 16-byte aligned images and "
+                       "NT a multiple of 16 bytes, at most 256 (N=%d NT=%d)",
+                  i, p.N, p.NT);
+        return IQA_ERR_UNSUPPORTED;
+    }
+    return IQA_OK;
+}
+
+// (Re)build the descriptor table for cfg and upload it.
+static iqa_status plan_build(iqa_plan *pl, const TileConfig &cfg)
+{
+    iqa_ctx *ctx = pl->ctx;
+    std::string why;
+    const int n = (int)pl->pairs.size();
+    long long units = 0;
+    for (int i = 0; i < n; ++i) {
+        const iqa_pair &p = pl->pairs[i];
+        TileConfig c = cfg;
+        c.TX = batch_tiles_across(p.N, p.NT, pl->dtype, cfg.threads);
+        if (!stream_config_valid(p.N, p.NT, pl->dtype, c, &why)) {
+            set_error(ctx, "pair %d (N=%d NT=%d): %s", i, p.N, p.NT, why.c_str());
+            return IQA_ERR_INVALID_ARG;
+        }
+        iqa_status s = fill_pair_desc(ctx, &pl->h_table[i], p.x, p.y, p.N, p.NT, pl->dtype,
+                                      c, pl->P, p.lisi_map, p.aug_map, p.sums, units);
+        if (s != IQA_OK) return s;
+        units += pair_units(p.N, p.NT, c);
+    }
+    cudaError_t e = cudaMemcpy(pl->d_table, pl->h_table, pl->table_bytes,
+                               cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "descriptor upload");
+    pl->cfg = cfg;
+    pl->total_units = units;
+    pl->grid = stream_grid(ctx, cfg, units);
+    return IQA_OK;
+}
+
+static StreamParams plan_params(const iqa_plan *pl)
+{
+    StreamParams sp;
+    std::memset(&sp, 0, sizeof sp);
+    sp.descs = pl->d_table;
+    sp.npairs = (int)pl->pairs.size();
+    sp.stage_bytes = pl->cfg.stage_kb * 1024;
+    sp.stages = pl->cfg.stages;
+    sp.total_units = pl->total_units;
+    sp.status = pl->ctx->d_status;
+    sp.timeout_ns = pl->ctx->wait_timeout_ns;
+    sp.sched = pl->d_sched;
+    sp.inject_stall = pl->ctx->inject_stall;
+    return sp;
+}
+
+static cudaError_t plan_launch_direct(iqa_plan *pl, cudaStream_t st)
+{
+    StreamParams sp = plan_params(pl);
+    return launch_stream(sp, pl->dtype, pl->cfg, pl->maps, pl->grid, st);
+}
+
+static void plan_drop_graph(iqa_plan *pl)
+{
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    pl->exec = nullptr;
+    pl->graph = nullptr;
+}
+
+static iqa_status plan_capture(iqa_plan *pl)
+{
+    plan_drop_graph(pl);
+    cudaStream_t s = pl->ctx->s_comp;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(pl->ctx, e, "graph capture begin");
+    cudaError_t el = plan_launch_direct(pl, s);
+    e = cudaStreamEndCapture(s, &pl->graph);
+    if (el != cudaSuccess) {
+        plan_drop_graph(pl);
+        return cuda_fail(pl->ctx, el, "captured launch");
+    }
+    if (e != cudaSuccess) return cuda_fail(pl->ctx, e, "graph capture end");
+    e = cudaGraphInstantiate(&pl->exec, pl->graph, 0);
+    if (e != cudaSuccess) {
+        plan_drop_graph(pl);
+        return cuda_fail(pl->ctx, e, "graph instantiate");
+    }
+    return IQA_OK;
+}
+
+TileConfig default_batch_config()
+{
+    TileConfig c;
+    c.variant = 1;
+    c.threads = 256;
+    c.stages = 3;
+    c.stage_kb = 16;
+    c.ctas_per_sm = 2;
+    return c;
+}
+
+}  // namespace iqa
+
+extern "C" {
+
+iqa_status iqa_plan_create(iqa_ctx *ctx, const iqa_pair *pairs, int npairs, iqa_dtype dtype,
+                           const iqa_params *params, int flags, iqa_plan **out)
+{
+    if (!ctx) return IQA_ERR_INVALID_ARG;
+    if (!out || !pairs || npairs < 1) {
+        set_error(ctx, "need out, pairs and npairs >= 1");
+        return IQA_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (!dtype_ok(dtype)) {
+        set_error(ctx, "unknown dtype %d", (int)dtype);
+        return IQA_ERR_INVALID_ARG;
+    }
+    iqa_params P;
+    iqa_status s = resolve_params(ctx, params, &P);
+    if (s != IQA_OK) return s;
+    for (int i = 0; i < npairs; ++i) {
+        s = check_pair(ctx, pairs[i], dtype, i);
+        if (s != IQA_OK) return s;
+    }
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+
+    iqa_plan *pl = new iqa_plan();
+    pl->ctx = ctx;
+    pl->dtype = dtype;
+    pl->P = P;
+    pl->flags = flags;
+    // largest units first, so the dynamic schedule ends evenly
+    std::vector<int> order(npairs);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return pairs[a].NT > pairs[b].NT;
+    });
+    int maps = 0;
+    for (int i : order) {
+        pl->pairs.push_back(pairs[i]);
+        const iqa_pair &p = pairs[i];
+        if (p.sums) maps = MAPS_AB;
+        if (p.lisi_map) maps |= MAPS_A;
+        if (p.aug_map) maps |= MAPS_B;
+        pl->input_bytes += 2ull * p.N * p.N * elem_size(dtype);
+    }
+    pl->maps = maps;
+    pl->table_bytes = sizeof(PairDesc) * (size_t)npairs;
+    pl->h_table = static_cast<PairDesc *>(
+        ::operator new(pl->table_bytes, std::align_val_t(alignof(PairDesc))));
+    const size_t need = pl->table_bytes + 256;
+    if (ctx->budget && need > ctx->budget) {
+        set_error(ctx, "plan tables need %zu bytes, over the HBM budget", need);
+        iqa_plan_destroy(pl);
+        cudaSetDevice(prev);
+        return IQA_ERR_NOMEM;
+    }
+    cudaError_t e = cudaMalloc(&pl->d_table, pl->table_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_sched, 256);
+    if (e == cudaSuccess) e = cudaMemset(pl->d_sched, 0, 256);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(ctx, "plan allocation failed: %s", cudaGetErrorString(e));
+        iqa_plan_destroy(pl);
+        cudaSetDevice(prev);
+        return IQA_ERR_NOMEM;
+    }
+    TileConfig cfg = default_batch_config();
+    {
+        std::lock_guard<std::mutex> g(ctx->cfg_mu);
+        if (ctx->has_batch_cfg[dtype]) cfg = ctx->batch_cfg[dtype];
+    }
+    s = plan_build(pl, cfg);
+    if (s == IQA_OK && (flags & IQA_PLAN_GRAPH)) s = plan_capture(pl);
+    cudaSetDevice(prev);
+    if (s != IQA_OK) {
+        iqa_plan_destroy(pl);
+        return s;
+    }
+    *out = pl;
+    return IQA_OK;
+}
+
+iqa_status iqa_plan_launch(iqa_plan *plan, iqa_stream stream)
+{
+    if (!plan) return IQA_ERR_INVALID_ARG;
+    cudaError_t e = plan->exec ? cudaGraphLaunch(plan->exec, (cudaStream_t)stream)
+                               : plan_launch_direct(plan, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(plan->ctx, e, "plan launch");
+    return IQA_OK;
+}
+
+void iqa_plan_destroy(iqa_plan *plan)
+{
+    if (!plan) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(plan->ctx->device);
+    plan_drop_graph(plan);
+    if (plan->d_table) cudaFree(plan->d_table);
+    if (plan->d_sched) cudaFree(plan->d_sched);
+    cudaSetDevice(prev);
+    if (plan->h_table)
+        ::operator delete(plan->h_table, std::align_val_t(alignof(PairDesc)));
+    delete plan;
+}
+
+iqa_status iqa_plan_info(const iqa_plan *plan, iqa_plan_stats *out)
+{
+    if (!plan || !out) return IQA_ERR_INVALID_ARG;
+    out->npairs = (int)plan->pairs.size();
+    out->total_units = plan->total_units;
+    out->grid = plan->grid;
+    out->input_bytes = plan->input_bytes;
+    out->graph = plan->exec ? 1 : 0;
+    out->config.variant = 1;
+    out->config.threads = plan->cfg.threads;
+    out->config.ilp = 0;
+    out->config.tiles_across = 0;
+    out->config.split = 1;
+    out->config.vector = 1;
+    out->config.stages = plan->cfg.stages;
+    out->config.stage_kb = plan->cfg.stage_kb;
+    out->config.ctas_per_sm = plan->cfg.ctas_per_sm;
+    return IQA_OK;
+}
+
+iqa_status iqa_plan_autotune(iqa_plan *plan, iqa_stream stream, int iters,
+                             iqa_launch_config *best_out)
+{
+    if (!plan || iters < 1) return IQA_ERR_INVALID_ARG;
+    iqa_ctx *ctx = plan->ctx;
+    const TileConfig keep = plan->cfg;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    TileConfig best = keep;
+    const int threads_c[] = {128, 256, 512};
+    const int shape_c[][3] = {{3, 16, 2}, {6, 8, 2}, {4, 16, 1}, {8, 8, 1},
+                              {12, 8, 1}, {5, 16, 1}, {2, 16, 2}, {4, 8, 2}};
+    iqa_status s = IQA_OK;
+    for (int th : threads_c) {
+        for (const auto &sh : shape_c) {
+            TileConfig c = keep;
+            c.threads = th;
+            c.stages = sh[0];
+            c.stage_kb = sh[1];
+            c.ctas_per_sm = sh[2];
+            if (plan_build(plan, c) != IQA_OK) continue;
+            cudaError_t e = plan_launch_direct(plan, (cudaStream_t)stream);  // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, (cudaStream_t)stream);
+            for (int i = 0; i < iters && e == cudaSuccess; ++i)
+                e = plan_launch_direct(plan, (cudaStream_t)stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, (cudaStream_t)stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                s = cuda_fail(ctx, e, "autotune launch");
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        if (s != IQA_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    iqa_status s2 = plan_build(plan, s == IQA_OK ? best : keep);
+    if (s == IQA_OK) s = s2;
+    if (s == IQA_OK && plan->exec) s = plan_capture(plan);
+    if (s == IQA_OK) {
+        std::lock_guard<std::mutex> g(ctx->cfg_mu);
+        ctx->batch_cfg[plan->dtype] = plan->cfg;
+        ctx->has_batch_cfg[plan->dtype] = true;
+    }
+    if (s == IQA_OK && best_out) {
+        iqa_plan_stats st;
+        iqa_plan_info(plan, &st);
+        *best_out = st.config;
+    }
+    return s;
+}
+
+}  // extern "C"

@@ -19,6 +19,11 @@ struct iqa_ctx {
     int l2_bytes = 0;
     int cc_major = 0, cc_minor = 0;
 
+    // device error word written by bounded waits in the persistent kernels
+    int *d_status = nullptr;
+    long long wait_timeout_ns = 1000000000LL;
+    int inject_stall = 0;  // test hook, see IQA_OPT_INJECT_STALL
+
     std::mutex err_mu;
     std::string last_error;
 
@@ -26,6 +31,9 @@ struct iqa_ctx {
     // keyed by (dtype, N, NT, maps)
     std::mutex cfg_mu;
     std::map<std::tuple<int, int, int, int>, iqa::TileConfig> pinned;
+    // batched-kernel shape per dtype, set by iqa_plan_autotune
+    iqa::TileConfig batch_cfg[3];
+    bool has_batch_cfg[3] = {false, false, false};
 
     // workspace of the host-buffer path (iqa_both_host)
     std::mutex host_mu;
@@ -52,6 +60,23 @@ TileConfig pick_config(iqa_ctx *ctx, int N, int NT, iqa_dtype dtype, int maps,
                        bool aligned);
 cudaError_t launch_tiles(const TileArgs &p, const TileConfig &c, iqa_dtype dtype,
                          int maps, int rows, cudaStream_t st);
+struct PairDesc;
+bool stream_config_valid(int N, int NT, iqa_dtype dtype, const TileConfig &c,
+                         std::string *why);
+TileConfig default_stream_config(int N, int NT, iqa_dtype dtype);
+iqa_status fill_pair_desc(iqa_ctx *ctx, PairDesc *d, const void *x, const void *y, int N,
+                          int NT, iqa_dtype dtype, const TileConfig &c, const iqa_params &P,
+                          float *lisi, float *aug, double *sums, long long unit_begin);
+long long pair_units(int N, int NT, const TileConfig &c);
+int stream_grid(iqa_ctx *ctx, const TileConfig &c, long long units);
+iqa_status run_stream_pair(iqa_ctx *ctx, const void *x, const void *y, iqa_dtype dtype,
+                           int N, int NT, const TileConfig &c, const iqa_params &P,
+                           float *lisi, float *aug, double *sums, int maps,
+                           cudaStream_t st);
+cudaError_t launch_stream(const StreamParams &sp, iqa_dtype dtype, const TileConfig &c,
+                          int maps, int grid, cudaStream_t st);
+bool any_config_valid(int N, int NT, iqa_dtype dtype, const TileConfig &c,
+                      std::string *why);
 TileArgs make_args(const void *x, const void *y, int N, int NT,
                    const TileConfig &c, const iqa_params &P, float *lisi,
                    float *aug, double *sums);

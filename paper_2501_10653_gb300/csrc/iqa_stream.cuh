@@ -1,0 +1,407 @@
+// iqa_stream.cuh -- persistent, TMA-pipelined form of the tile reduction.
+//
+// Same method as iqa_tiles.cuh (arxiv 2501.10653, Section 2, Eq. 1 and Eq. 2:
+// clamp, tile, four per-tile sums, per-tile ratios), laid out for GB300:
+//   * one CTA per SM slot loops over units (TX whole tiles across x N_T rows)
+//     of one or many image pairs, fetched from a global counter (dynamic) or
+//     taken round-robin (static); the producer tells the consumers which unit
+//     a stage holds through a per-stage slot in shared memory;
+//   * a producer warp streams every unit in chunks of CH rows with 2-D TMA
+//     tensor copies (cp.async.bulk.tensor) of x and y into a ring of shared-
+//     memory stages, signalling completion on per-stage mbarriers;
+//   * consumer warps read each stage with 16-byte shared loads, clamp, form
+//     the terms, accumulate in registers across the unit's chunks, release the
+//     stage, and reduce the unit (shuffle trees, a named barrier) while the
+//     producer is already several chunks ahead;
+//   * every mbarrier wait is bounded by a time limit: on expiry the CTA
+//     records an error code, stops issuing, waits (bounded) for the copies it
+//     has in flight and returns, so the host sees a status instead of a hang.
+#pragma once
+
+#include <cuda.h>
+
+#include "iqa_device.cuh"
+#include "iqa_internal.h"
+
+namespace iqa {
+
+// One image pair of a persistent launch.  Lives in global memory (batched
+// launches) or inside the kernel's __grid_constant__ parameter (one pair);
+// the CUtensorMap members give it the alignment the TMA unit requires.
+struct PairDesc {
+    CUtensorMap tmx;         // 2-D map of x: dims {N, N}, box {BW, CH}
+    CUtensorMap tmy;         // same for y
+    float *lisi;
+    float *aug;
+    double *sums;
+    long long unit_begin;    // first global unit index of this pair
+    int N, NT, T;            // image side, tile side, tiles per row
+    int TX;                  // tiles across a unit
+    int units_x;             // units per tile row = T / TX
+    int CH;                  // rows per chunk
+    int chunks;              // chunks per unit = NT / CH
+    int LPU;                 // 16-byte vectors per unit row = TX * NT / VEC
+    int LPT;                 // vectors per tile row = NT / VEC
+    int pad_;
+    float C1f, C2f, Cf, Df;
+};
+
+struct StreamParams {
+    const PairDesc *descs;   // table in global memory, or nullptr: use one_pair
+    int npairs;
+    int stage_bytes;         // bytes of ONE image per stage
+    int stages;
+    int pad_;
+    long long total_units;
+    int *status;             // error word (nullable), nonzero = failed
+    long long timeout_ns;    // bound on every wait
+    // Dynamic schedule (nullable: static round-robin instead): [0] = next
+    // unit, [1] = CTAs done fetching.  Zero before the launch; the last CTA to
+    // finish fetching puts both back to zero, so a stream of launches needs no
+    // reset in between (launches sharing a counter must not overlap).
+    unsigned long long *sched;
+    int inject_stall;        // test hook: 1 = the producer issues nothing
+    int pad2_;
+    PairDesc one_pair;
+};
+
+enum StreamError { STREAM_TIMEOUT_FULL = 1, STREAM_TIMEOUT_EMPTY = 2 };
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait on the phase with the given parity.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          long long timeout_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if ((long long)(global_ns() - t0) > timeout_ns) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// 2-D tiled TMA load of one box at (col, row) into shared memory.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int col,
+                                            int row, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(col), "r"(row), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+__device__ __forceinline__ void named_bar(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Which pair owns global unit u (pairs are stored in unit order).
+__device__ __forceinline__ int find_pair(const PairDesc *d, int npairs, long long u)
+{
+    int lo = 0, hi = npairs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (d[mid].unit_begin <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Consumer-side reduction of one unit over the CT consumer threads, with
+// named barrier 1 (the producer warp does not take part).  Same order and
+// layout as reduce_unit in iqa_device.cuh.
+template <int CT>
+__device__ __forceinline__ void reduce_unit_consumers(const float (&acc)[4], int TX,
+                                                      int LPU, int LPT, float (*red)[CT],
+                                                      float *part)
+{
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    constexpr int WARPS = CT / 32;
+    if (TX == 1) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float v = warp_sum(acc[k]);
+            if (lane == 0) red[k][warp] = v;
+        }
+        named_bar(1, CT);
+        if (warp == 0) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float v = lane < WARPS ? red[k][lane] : 0.0f;
+                v = warp_sum(v);
+                if (lane == 0) part[k] = v;
+            }
+        }
+        named_bar(1, CT);
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[k][tid] = acc[k];
+    named_bar(1, CT);
+    const int count = (CT / LPU) * LPT;
+    for (int tl = warp; tl < TX; tl += WARPS) {
+        float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int e = lane; e < count; e += 32) {
+            int q = e / LPT;
+            int src = q * LPU + tl * LPT + (e - q * LPT);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s[k] += red[k][src];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float v = warp_sum(s[k]);
+            if (lane == 0) part[tl * 4 + k] = v;
+        }
+    }
+    named_bar(1, CT);
+}
+
+__device__ __forceinline__ void write_tile_desc(const PairDesc &d, long long t, float A,
+                                                float B, float Sx, float Sy)
+{
+    if (d.lisi) d.lisi[t] = __fdiv_rn(d.Df * A, fmaxf(Sx, Sy) + d.C2f);
+    if (d.aug) d.aug[t] = 1.0f - __fdiv_rn(B, (Sx + Sy) + d.Cf);
+    if (d.sums) {
+        double *o = d.sums + 4 * t;
+        o[0] = A;
+        o[1] = B;
+        o[2] = Sx;
+        o[3] = Sy;
+    }
+}
+
+// Dynamic shared memory layout: [stages][2][stage_bytes] ring, then the
+// 2*stages mbarriers, the per-stage unit slots, the reduction scratch
+// red[4][CT] and part[kMaxTX*4], and the abort flag.  Host:
+// stream_smem_bytes().
+template <typename T, int CT, bool DO_A, bool DO_B>
+__global__ void __launch_bounds__(CT + 32, 1)
+    iqa_stream_kernel(const __grid_constant__ StreamParams sp)
+{
+    constexpr int VEC = Elem<T>::VEC;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int S = sp.stages;
+    const int SB = sp.stage_bytes;
+    unsigned char *ring = smem;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)S * 2 * SB);
+    uint64_t *empty = full + S;
+    long long *stage_unit = reinterpret_cast<long long *>(empty + S);
+    float(*red)[CT] = reinterpret_cast<float(*)[CT]>(stage_unit + S);
+    float *part = reinterpret_cast<float *>(red + 4);
+    int *abort_flag = reinterpret_cast<int *>(part + kMaxTX * 4);
+
+    const PairDesc *descs = sp.descs ? sp.descs : &sp.one_pair;
+    const int tid = threadIdx.x;
+    const bool producer = tid >= CT;
+
+    if (tid == 0) {
+        *abort_flag = 0;
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], CT / 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (producer) {
+        // ---------------- producer warp: one elected lane issues the copies
+        if (tid != CT) return;
+        long long k = 0;  // chunk counter of this CTA
+        int last_pair = -1;
+        bool ok = true;
+        long long u = blockIdx.x, u_next = -1, i = 0;
+        if (sp.inject_stall) ok = false;  // test hook: issue nothing at all
+        else if (sp.sched) u = (long long)atomicAdd(&sp.sched[0], 1ull);
+        while (ok) {
+            // the next unit's index is fetched before this unit's copies are
+            // issued, so the atomic's latency hides behind them
+            if (u < sp.total_units) {
+                if (sp.sched) u_next = (long long)atomicAdd(&sp.sched[0], 1ull);
+                else u_next = blockIdx.x + (++i) * (long long)gridDim.x;
+            }
+            const bool last = u >= sp.total_units;
+            const int pi = (!last && sp.npairs > 1) ? find_pair(descs, sp.npairs, u) : 0;
+            const PairDesc &d = descs[pi];
+            const int nchunks = last ? 1 : d.chunks;
+            long long lu = 0;
+            int col0 = 0, row0 = 0;
+            uint32_t bytes = 0;
+            if (!last) {
+                if (pi != last_pair) {
+                    prefetch_tmap(&d.tmx);
+                    prefetch_tmap(&d.tmy);
+                    last_pair = pi;
+                }
+                lu = u - d.unit_begin;
+                const int trow = (int)(lu / d.units_x);
+                col0 = (int)(lu - (long long)trow * d.units_x) * d.TX * d.NT;
+                row0 = trow * d.NT;
+                bytes = (uint32_t)(d.CH * d.TX * d.NT * (int)sizeof(T));
+            }
+            for (int c = 0; c < nchunks; ++c, ++k) {
+                const int s = (int)(k % S);
+                const uint32_t par = (uint32_t)((k / S) & 1) ^ 1u;
+                if (!mbar_wait(&empty[s], par, sp.timeout_ns)) {
+                    if (sp.status) atomicOr(sp.status, STREAM_TIMEOUT_EMPTY);
+                    atomicExch(abort_flag, 1);
+                }
+                if (*((volatile int *)abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                if (last) {
+                    // end of work: an empty stage whose unit slot says so
+                    stage_unit[s] = -1;
+                    mbar_arrive(&full[s]);
+                    break;
+                }
+                stage_unit[s] = u;
+                mbar_expect_tx(&full[s], 2 * bytes);
+                unsigned char *dst = ring + (size_t)s * 2 * SB;
+                tma_load_2d(dst, &d.tmx, col0, row0 + c * d.CH, &full[s]);
+                tma_load_2d(dst + SB, &d.tmy, col0, row0 + c * d.CH, &full[s]);
+            }
+            if (last) break;
+            u = u_next;
+        }
+        if (sp.sched) {
+            // every CTA has made its final fetch once the count reaches the
+            // grid size; the last one puts the counters back to zero
+            if (atomicAdd(&sp.sched[1], 1ull) == (unsigned long long)gridDim.x - 1) {
+                atomicExch(&sp.sched[0], 0ull);
+                atomicExch(&sp.sched[1], 0ull);
+            }
+        }
+        // Copies still in flight when leaving (only after an abort): wait,
+        // bounded, for every stage's last issued phase before returning.
+        if (!ok && k > 0) {
+            for (long long j = (k > S ? k - S : 0); j < k; ++j)
+                mbar_wait(&full[j % S], (uint32_t)((j / S) & 1), sp.timeout_ns);
+        }
+        return;
+    }
+
+    // -------------------- consumer warps
+    // Every consumer thread waits (bounded) for each chunk itself, then all
+    // consumers meet at named barrier 2 and read the shared abort flag, so a
+    // timeout anywhere makes every consumer leave at the same point and no
+    // thread is ever left waiting at a barrier the others skipped.
+    const int lane = tid & 31;
+    const PairDesc *d = nullptr;
+    long long u = -1, lu = 0;
+    int c = 0, V = 0;
+    Kahan ka, kb, kx, ky;
+    for (long long k = 0;; ++k) {
+        const int s = (int)(k % S);
+        if (!mbar_wait(&full[s], (uint32_t)((k / S) & 1), sp.timeout_ns)) {
+            if (sp.status) atomicOr(sp.status, STREAM_TIMEOUT_FULL);
+            atomicExch(abort_flag, 1);
+        }
+        named_bar(2, CT);
+        if (*((volatile int *)abort_flag)) return;
+        if (c == 0) {
+            u = stage_unit[s];
+            if (u < 0) return;
+            d = &descs[sp.npairs > 1 ? find_pair(descs, sp.npairs, u) : 0];
+            lu = u - d->unit_begin;
+            V = d->CH * d->LPU;
+            ka = Kahan();
+            kb = Kahan();
+            kx = Kahan();
+            ky = Kahan();
+        }
+        const uint4 *xs = reinterpret_cast<const uint4 *>(ring + (size_t)s * 2 * SB);
+        const uint4 *ys = reinterpret_cast<const uint4 *>(ring + (size_t)s * 2 * SB + SB);
+        const float C1f = d->C1f;
+        float ba = 0.0f, bb = 0.0f, bx = 0.0f, by = 0.0f;
+        for (int v = tid; v < V; v += CT) {
+            Raw<T, VEC> rx, ry;
+            rx.v = xs[v];
+            ry.v = ys[v];
+            float xv[VEC], yv[VEC];
+            unpack<T, VEC>(rx, xv);
+            unpack<T, VEC>(ry, yv);
+            float a, b, sx, sy;
+            pixel_terms<VEC, DO_A, DO_B>(xv, yv, C1f, a, b, sx, sy);
+            ba += a;
+            bb += b;
+            bx += sx;
+            by += sy;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (DO_A) ka.add(ba);
+        if (DO_B) kb.add(bb);
+        kx.add(bx);
+        ky.add(by);
+        if (++c == d->chunks) {
+            c = 0;
+            float acc[4] = {ka.value(), kb.value(), kx.value(), ky.value()};
+            reduce_unit_consumers<CT>(acc, d->TX, d->LPU, d->LPT, red, part);
+            const int trow = (int)(lu / d->units_x);
+            const int ucol = (int)(lu - (long long)trow * d->units_x);
+            const long long t0 = (long long)trow * d->T + (long long)ucol * d->TX;
+            for (int tl = tid; tl < d->TX; tl += CT)
+                write_tile_desc(*d, t0 + tl, part[tl * 4 + 0], part[tl * 4 + 1],
+                                part[tl * 4 + 2], part[tl * 4 + 3]);
+        }
+    }
+}
+
+inline size_t stream_smem_bytes(int stages, int stage_bytes, int ct)
+{
+    return (size_t)stages * 2 * stage_bytes + (size_t)2 * stages * 8 + (size_t)stages * 8 +
+           (size_t)4 * ct * 4 + (size_t)kMaxTX * 4 * 4 + 16;
+}
+
+}  // namespace iqa

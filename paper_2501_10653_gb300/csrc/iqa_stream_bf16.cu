@@ -1,0 +1,13 @@
+// iqa_stream_bf16.cu -- persistent TMA-pipelined kernels for __nv_bfloat16 pixel storage.
+#include "iqa_stream.cuh"
+#include "iqa_stream_launch.cuh"
+
+namespace iqa {
+
+cudaError_t launch_stream_bf16(const StreamParams &sp, int ct, int maps, int grid,
+                              size_t smem, cudaStream_t st)
+{
+    return launch_stream_t<__nv_bfloat16>(sp, ct, maps, grid, smem, st);
+}
+
+}  // namespace iqa

@@ -1,0 +1,55 @@
+// iqa_stream_launch.cuh -- host-side launch of iqa_stream_kernel for one
+// storage type (included by iqa_stream_<type>.cu).
+#pragma once
+
+#include "iqa_internal.h"
+#include "iqa_stream.cuh"
+
+namespace iqa {
+
+template <typename T, int CT, bool A, bool B>
+static cudaError_t stream_launch_one(const StreamParams &sp, int grid, size_t smem,
+                                     cudaStream_t st)
+{
+    auto kern = iqa_stream_kernel<T, CT, A, B>;
+    // raise the dynamic shared-memory limit once per instantiation
+    static size_t allowed = 0;
+    if (smem > allowed) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        allowed = smem;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3(CT + 32, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.numAttrs = 0;
+    return cudaLaunchKernelEx(&cfg, kern, sp);
+}
+
+template <typename T, int CT>
+static cudaError_t stream_by_maps(const StreamParams &sp, int maps, int grid, size_t smem,
+                                  cudaStream_t st)
+{
+    switch (maps) {
+    case MAPS_A: return stream_launch_one<T, CT, true, false>(sp, grid, smem, st);
+    case MAPS_B: return stream_launch_one<T, CT, false, true>(sp, grid, smem, st);
+    default: return stream_launch_one<T, CT, true, true>(sp, grid, smem, st);
+    }
+}
+
+template <typename T>
+static cudaError_t launch_stream_t(const StreamParams &sp, int ct, int maps, int grid,
+                                   size_t smem, cudaStream_t st)
+{
+    switch (ct) {
+    case 128: return stream_by_maps<T, 128>(sp, maps, grid, smem, st);
+    case 256: return stream_by_maps<T, 256>(sp, maps, grid, smem, st);
+    case 512: return stream_by_maps<T, 512>(sp, maps, grid, smem, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace iqa

@@ -55,13 +55,36 @@ class iqa_params(ctypes.Structure):
 
 
 class iqa_launch_config(ctypes.Structure):
-    _fields_ = [("threads", ctypes.c_int), ("ilp", ctypes.c_int),
-                ("tiles_across", ctypes.c_int), ("split", ctypes.c_int),
-                ("vector", ctypes.c_int), ("variant", ctypes.c_int)]
+    _fields_ = [("variant", ctypes.c_int), ("threads", ctypes.c_int),
+                ("ilp", ctypes.c_int), ("tiles_across", ctypes.c_int),
+                ("split", ctypes.c_int), ("vector", ctypes.c_int),
+                ("stages", ctypes.c_int), ("stage_kb", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
+
+class iqa_pair(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("N", ctypes.c_int),
+                ("NT", ctypes.c_int), ("lisi_map", ctypes.c_void_p),
+                ("aug_map", ctypes.c_void_p), ("sums", ctypes.c_void_p)]
+
+
+class iqa_plan_stats(ctypes.Structure):
+    _fields_ = [("npairs", ctypes.c_int), ("total_units", ctypes.c_longlong),
+                ("grid", ctypes.c_int), ("input_bytes", ctypes.c_ulonglong),
+                ("graph", ctypes.c_int), ("config", iqa_launch_config)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "config"}
+        d["config"] = self.config.as_dict()
+        return d
+
+
+IQA_PLAN_GRAPH = 1
+IQA_OPT_WAIT_TIMEOUT_US = 1
+IQA_OPT_INJECT_STALL = 2
 
 _lib = None
 _vp = ctypes.c_void_p
@@ -84,6 +107,13 @@ def _declare(lib):
         "iqa_both_host": ([_vp, _vp, _vp, _i, _i, _i, P(iqa_params), _vp, _vp, _vp], _st),
         "iqa_get_config": ([_vp, _i, _i, _i, _i, P(iqa_launch_config)], _st),
         "iqa_set_config": ([_vp, _i, _i, _i, _i, P(iqa_launch_config)], _st),
+        "iqa_wait": ([_vp, _vp, _i], _st),
+        "iqa_set_option": ([_vp, _i, ctypes.c_longlong], _st),
+        "iqa_plan_create": ([_vp, P(iqa_pair), _i, _i, P(iqa_params), _i, P(_vp)], _st),
+        "iqa_plan_launch": ([_vp, _vp], _st),
+        "iqa_plan_destroy": ([_vp], None),
+        "iqa_plan_info": ([_vp, P(iqa_plan_stats)], _st),
+        "iqa_plan_autotune": ([_vp, _vp, _i, P(iqa_launch_config)], _st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -204,6 +234,67 @@ def iqa_set_config(ctx, dtype, N, NT, maps, cfg):
         ref = None
     else:
         if isinstance(cfg, dict):
-            cfg = iqa_launch_config(**cfg)
+            full = {"variant": 0, "threads": 256, "ilp": 4, "tiles_across": 1,
+                    "split": 1, "vector": 1, "stages": 8, "stage_kb": 8,
+                    "ctas_per_sm": 1}
+            full.update(cfg)
+            cfg = iqa_launch_config(**full)
         ref = ctypes.byref(cfg)
     return _check(ctx, lib().iqa_set_config(ctx, dtype, N, NT, maps, ref))
+
+
+def iqa_wait(ctx, stream=None, timeout_us=-1):
+    return _check(ctx, lib().iqa_wait(ctx, _stream(stream), int(timeout_us)))
+
+
+def iqa_set_option(ctx, option, value):
+    return _check(ctx, lib().iqa_set_option(ctx, int(option), int(value)))
+
+
+def make_pair(x, y, N, NT, lisi_map=None, aug_map=None, sums=None):
+    """An iqa_pair from tensors / addresses (marshalling helper)."""
+    return iqa_pair(_ptr(x), _ptr(y), int(N), int(NT), _ptr(lisi_map), _ptr(aug_map),
+                    _ptr(sums))
+
+
+class _Plan:
+    """Owner of an iqa_plan handle; keeps the pair array alive."""
+
+    def __init__(self, ctx, handle, pairs):
+        self.ctx = ctx
+        self.handle = handle
+        self._pairs = pairs
+
+    def __int__(self):
+        return self.handle
+
+
+def iqa_plan_create(ctx, pairs, dtype, params=None, flags=IQA_PLAN_GRAPH):
+    arr = (iqa_pair * len(pairs))(*pairs)
+    h = _vp()
+    _check(ctx, lib().iqa_plan_create(ctx, arr, len(pairs), int(dtype), _params(params),
+                                      int(flags), ctypes.byref(h)))
+    return _Plan(ctx, h.value, arr)
+
+
+def iqa_plan_launch(plan, stream=None):
+    return _check(plan.ctx, lib().iqa_plan_launch(plan.handle, _stream(stream)))
+
+
+def iqa_plan_destroy(plan):
+    if plan.handle:
+        lib().iqa_plan_destroy(plan.handle)
+        plan.handle = None
+
+
+def iqa_plan_info(plan):
+    st = iqa_plan_stats()
+    _check(plan.ctx, lib().iqa_plan_info(plan.handle, ctypes.byref(st)))
+    return st
+
+
+def iqa_plan_autotune(plan, stream=None, iters=5):
+    best = iqa_launch_config()
+    _check(plan.ctx, lib().iqa_plan_autotune(plan.handle, _stream(stream), int(iters),
+                                             ctypes.byref(best)))
+    return best

@@ -1,0 +1,180 @@
+"""Batched form (one persistent launch over many pairs), through the C-ABI
+plan API, against the FP64 oracle (needs a GPU)."""
+import numpy as np
+import pytest
+
+import parity
+from paper_2501_10653_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+PARAMS = {"C1": 1e-6, "C2": 1e-6, "C": 1e-6, "D": 0.0}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2501_10653_gb300 import build, iqa
+    build.build()
+    h = iqa.iqa_create(0, 0)
+    yield h
+    iqa.iqa_destroy(h)
+
+
+def _specs():
+    # a small stand-in for the mixed batch: N from {256, 512, 1024}, N_T from
+    # {32, 64, 128}, several tiles per unit and several chunks per unit
+    return [(1024, 64), (256, 32), (512, 128), (1024, 32), (512, 64), (256, 128),
+            (1024, 128), (512, 32), (256, 64), (1024, 64), (768, 96), (640, 80)]
+
+
+class Batch:
+    def __init__(self, specs, dtype="f32", seed=2):
+        import torch
+        self.specs = specs
+        self.host = [synth.mixed_batch_pair(i, N, seed=seed, dtype=dtype)
+                     for i, (N, _) in enumerate(specs)]
+        self.dev = [(parity.to_device(x), parity.to_device(y)) for x, y in self.host]
+        self.out = []
+        for N, NT in specs:
+            T = N // NT
+            self.out.append((torch.full((T * T,), float("nan"), device="cuda"),
+                             torch.full((T * T,), float("nan"), device="cuda"),
+                             torch.full((T * T, 4), float("nan"), device="cuda",
+                                        dtype=torch.float64)))
+
+    def pairs(self, idx=None):
+        from paper_2501_10653_gb300 import iqa
+        idx = range(len(self.specs)) if idx is None else idx
+        return [iqa.make_pair(self.dev[i][0], self.dev[i][1], self.specs[i][0],
+                              self.specs[i][1], *self.out[i]) for i in idx]
+
+    def results(self, i):
+        return tuple(t.cpu().numpy() for t in self.out[i])
+
+
+def _run(ctx, batch, idx=None, flags=1, dtype_code=0, launches=1):
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    plan = iqa.iqa_plan_create(ctx, batch.pairs(idx), dtype_code, PARAMS, flags)
+    try:
+        for _ in range(launches):
+            iqa.iqa_plan_launch(plan, torch.cuda.current_stream())
+        iqa.iqa_wait(ctx, torch.cuda.current_stream(), 20_000_000)
+        info = iqa.iqa_plan_info(plan)
+    finally:
+        iqa.iqa_plan_destroy(plan)
+    return info
+
+
+def test_mixed_batch_against_oracle(ctx, orc):
+    b = Batch(_specs())
+    info = _run(ctx, b)
+    assert info.npairs == len(b.specs) and info.graph == 1
+    for i, (N, NT) in enumerate(b.specs):
+        x, y = b.host[i]
+        want = parity.oracle_maps(orc, x, y, NT, PARAMS)
+        gl, ga, gs = b.results(i)
+        parity.assert_parity((gl.reshape(N // NT, -1), ga.reshape(N // NT, -1), gs),
+                             want, PARAMS)
+
+
+@pytest.mark.parametrize("dt,code", [("f16", 1), ("bf16", 2)])
+def test_mixed_batch_16bit(ctx, orc, dt, code):
+    b = Batch(_specs()[:6], dtype=dt)
+    _run(ctx, b, dtype_code=code)
+    for i, (N, NT) in enumerate(b.specs):
+        x, y = b.host[i]
+        want = parity.oracle_maps(orc, x, y, NT, PARAMS)
+        parity.assert_parity(b.results(i), want, PARAMS)
+
+
+def test_same_alone_and_in_the_mix(ctx):
+    """Each pair's maps are bit-identical whether it runs alone or with others."""
+    b = Batch(_specs())
+    _run(ctx, b)
+    mixed = [b.results(i) for i in range(len(b.specs))]
+    for i in (0, 3, 5, 10):
+        for t in b.out[i]:
+            t.fill_(float("nan"))
+        _run(ctx, b, idx=[i])
+        alone = b.results(i)
+        for u, v in zip(alone, mixed[i]):
+            assert np.array_equal(u, v), "pair %d differs alone vs in the mix" % i
+
+
+def test_graph_direct_and_repeated_launches_agree(ctx):
+    """Graph replay, direct launch and back-to-back launches (the work counter
+    resets itself) all give the same bits."""
+    b = Batch(_specs()[:8])
+    _run(ctx, b, flags=0)
+    direct = [b.results(i) for i in range(8)]
+    _run(ctx, b, flags=1, launches=4)
+    for i in range(8):
+        for u, v in zip(b.results(i), direct[i]):
+            assert np.array_equal(u, v)
+
+
+def test_plan_autotune_keeps_parity(ctx, orc):
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    b = Batch(_specs()[:6])
+    plan = iqa.iqa_plan_create(ctx, b.pairs(), 0, PARAMS, iqa.IQA_PLAN_GRAPH)
+    try:
+        best = iqa.iqa_plan_autotune(plan, torch.cuda.current_stream(), 2)
+        assert best.variant == 1 and best.threads in (128, 256, 512)
+        for t in b.out:
+            for u in t:
+                u.fill_(float("nan"))
+        iqa.iqa_plan_launch(plan, torch.cuda.current_stream())
+        iqa.iqa_wait(ctx, torch.cuda.current_stream(), 20_000_000)
+    finally:
+        iqa.iqa_plan_destroy(plan)
+    for i, (N, NT) in enumerate(b.specs):
+        x, y = b.host[i]
+        parity.assert_parity(b.results(i), parity.oracle_maps(orc, x, y, NT, PARAMS),
+                             PARAMS)
+
+
+def test_plan_rejects_bad_pairs(ctx):
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    d = torch.zeros(256 * 256 + 4, device="cuda")
+    m = torch.zeros(64, device="cuda")
+    bad = [iqa.make_pair(d, None, 256, 32, m),
+           iqa.make_pair(d, d, 256, 48, m),
+           iqa.make_pair(d[1:], d, 256, 32, m),
+           iqa.make_pair(d, d, 256, 32)]
+    for p in bad:
+        with pytest.raises(iqa.IqaError) as ei:
+            iqa.iqa_plan_create(ctx, [p], 0, PARAMS)
+        assert ei.value.status in (iqa.IQA_ERR_INVALID_ARG, iqa.IQA_ERR_UNSUPPORTED)
+
+
+def test_device_wait_timeout_reports_and_context_recovers(ctx, orc):
+    """Failure path without a GPU fault: the producer is told to issue nothing,
+    so every consumer wait runs out after 20 ms; the kernel records the error
+    and returns, iqa_wait reports IQA_ERR_TIMEOUT, and the next launch on the
+    same context is correct."""
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    b = Batch(_specs()[:3])
+    st = torch.cuda.current_stream()
+    plan = iqa.iqa_plan_create(ctx, b.pairs(), 0, PARAMS, 0)
+    try:
+        iqa.iqa_set_option(ctx, iqa.IQA_OPT_WAIT_TIMEOUT_US, 20_000)
+        iqa.iqa_set_option(ctx, iqa.IQA_OPT_INJECT_STALL, 1)
+        iqa.iqa_plan_launch(plan, st)
+        with pytest.raises(iqa.IqaError) as ei:
+            iqa.iqa_wait(ctx, st, 20_000_000)
+        assert ei.value.status == iqa.IQA_ERR_TIMEOUT
+        iqa.iqa_set_option(ctx, iqa.IQA_OPT_INJECT_STALL, 0)
+        iqa.iqa_set_option(ctx, iqa.IQA_OPT_WAIT_TIMEOUT_US, 1_000_000)
+        iqa.iqa_plan_launch(plan, st)
+        iqa.iqa_wait(ctx, st, 20_000_000)
+    finally:
+        iqa.iqa_set_option(ctx, iqa.IQA_OPT_INJECT_STALL, 0)
+        iqa.iqa_plan_destroy(plan)
+    for i, (N, NT) in enumerate(b.specs):
+        x, y = b.host[i]
+        parity.assert_parity(b.results(i), parity.oracle_maps(orc, x, y, NT, PARAMS),
+                             PARAMS)

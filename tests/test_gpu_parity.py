@@ -262,3 +262,56 @@ def test_bad_arguments_rejected(ctx):
         iqa.iqa_both(ctx, d, d, iqa.IQA_F32, 64, 16, None, None, None)
     assert ei.value.status == iqa.IQA_ERR_INVALID_ARG
     torch.cuda.synchronize()
+
+
+def _stream_configs(N, NT, es):
+    V = 16 // es
+    T = N // NT
+    for threads in (128, 256, 512):
+        for TX in [d for d in range(1, 65) if T % d == 0 and d * NT <= 256]:
+            for stage_kb in (2, 4, 8, 16):
+                for stages, cps in ((4, 1), (8, 1), (3, 2)):
+                    yield dict(variant=1, threads=threads, tiles_across=TX,
+                               stages=stages, stage_kb=stage_kb, ctas_per_sm=cps)
+
+
+@pytest.mark.parametrize("dt", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("N,NT", [(512, 16), (512, 64), (512, 256), (480, 48), (384, 128)])
+def test_tma_persistent_kernel_every_shape(ctx, orc, dt, N, NT):
+    """The persistent TMA-pipelined kernel (variant 1) against the oracle over
+    every valid launch shape: consumer counts, units of several tiles, stage
+    sizes that split a tile into 1..64 chunks, ring depths, 1 or 2 CTAs/SM."""
+    from paper_2501_10653_gb300 import iqa
+    es = 4 if dt == "f32" else 2
+    if NT % (16 // es):
+        pytest.skip("tile not a whole number of 16-byte vectors")
+    x, y = synth.paper_pair(N=N, dtype=dt)
+    want = parity.oracle_maps(orc, x, y, NT, PARAMS)
+    dx, dy = parity.to_device(x), parity.to_device(y)
+    code = parity.dtype_code(x)
+    n_ok = 0
+    for cfg in _stream_configs(N, NT, es):
+        try:
+            iqa.iqa_set_config(ctx, code, N, NT, iqa.MAPS_BOTH, cfg)
+        except iqa.IqaError as e:
+            assert e.status == iqa.IQA_ERR_INVALID_ARG
+            continue
+        got = parity.gpu_maps(ctx, x, y, NT, PARAMS, dx=dx, dy=dy)
+        iqa.iqa_wait(ctx, None, 10_000_000)
+        parity.assert_parity(got, want, PARAMS)
+        n_ok += 1
+    iqa.iqa_set_config(ctx, code, N, NT, iqa.MAPS_BOTH, None)
+    assert n_ok >= 3
+
+
+@pytest.mark.parametrize("which", ["lisi", "aug", "both_nosums"])
+def test_tma_kernel_single_maps(ctx, orc, paper, which):
+    from paper_2501_10653_gb300 import iqa
+    x, y = paper
+    maps = {"lisi": iqa.MAPS_LISI, "aug": iqa.MAPS_AUGLISI, "both_nosums": iqa.MAPS_BOTH}[which]
+    iqa.iqa_set_config(ctx, iqa.IQA_F32, 2048, 64, maps,
+                       dict(variant=1, threads=256, tiles_across=1, stages=8, stage_kb=8))
+    want = parity.oracle_maps(orc, x, y, 64, PARAMS)
+    got = parity.gpu_maps(ctx, x, y, 64, PARAMS, which)
+    iqa.iqa_set_config(ctx, iqa.IQA_F32, 2048, 64, maps, None)
+    parity.assert_parity(got, want, PARAMS)
