@@ -4,9 +4,11 @@
 Workload (the paper's Section 3 shape): N = 2048, N_T = 64 (1024 tiles), FP32
 storage, synthetic radio-sky pairs (33 Gaussian-beam sources, sigma 2e-4
 noise, 1e-4 diffuse ripple, the 5 faintest sources dropped in epoch 2).  One
-step = one ``iqa_both`` call through the C-ABI: both maps from a single read of
-each pixel of one pair.  Inputs rotate over a pool of distinct pairs larger
-than twice the L2 cache, so every step reads its pixels from HBM.
+step = one persistent launch (a replayed CUDA graph of ``iqa_plan_launch``)
+that computes both maps of B distinct such pairs from a single read of each
+pixel; B pairs are 33.5 MB each, far larger than the L2 cache, so every step
+reads its pixels from HBM.  The one-pair-per-launch form (``iqa_both``) is
+timed beside it.
 
 Prints ONE JSON line (rank 0).  ``value`` is the whole-job HBM throughput
 (algorithmic bytes 2 N^2 * 4 per pair) over the K timed steps; ``e2e`` is the
@@ -40,6 +42,7 @@ METRIC = ("LISI/augLISI HBM GB/s (% of peak) and pairs/s at N=2048,N_T=64; "
 N_IMG = 2048
 N_TILE = 64
 PARAMS = {"C1": 1e-6, "C2": 1e-6, "C": 1e-6, "D": 0.5e-6}
+PAPER_NT_SWEEP = (16, 32, 64, 128, 256)
 PAPER_H100 = {"lisi_kernel_ms": 0.101, "auglisi_kernel_ms": 0.091,
               "hardware": "H100", "note": "context only (another machine)"}
 
@@ -47,11 +50,11 @@ PAPER_H100 = {"lisi_kernel_ms": 0.101, "auglisi_kernel_ms": 0.091,
 def parse_args(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100000)
-    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--pool", type=int, default=10,
-                    help="distinct device pairs the steps rotate over")
+    ap.add_argument("--batch", type=int, default=16,
+                    help="distinct N=2048 pairs per step (one persistent launch)")
     ap.add_argument("--e2e-steps", type=int, default=60)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="bound on the CPU-baseline sample")
@@ -212,6 +215,29 @@ def _cpu_model():
 # --------------------------------------------------------------------------
 # our implementation
 
+def _pool_pairs(rank, count):
+    from paper_2501_10653_gb300 import synth
+    return [synth.paper_pair(pair_index=rank * count + i) for i in range(count)]
+
+
+def _time_plan(iqa, ctx, plan, stream, K, warmup):
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, warmup)):
+            iqa.iqa_plan_launch(plan, stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(K):
+            iqa.iqa_plan_launch(plan, stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    iqa.iqa_wait(ctx, stream, 60_000_000)
+    return e0.elapsed_time(e1)
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -223,71 +249,68 @@ def run_ours(args):
     if rank == 0 or world == 1:
         lib_build.build()
     barrier(world)
-    from paper_2501_10653_gb300 import iqa, synth
+    from paper_2501_10653_gb300 import iqa
 
     N, NT = N_IMG, N_TILE
     T = N // NT
+    B = max(1, args.batch)
     pair_bytes = 2 * N * N * 4
     ctx = iqa.iqa_create(local, 0)
     params = iqa.iqa_params(PARAMS["C1"], PARAMS["C2"], PARAMS["C"], PARAMS["D"])
+    stream = torch.cuda.Stream(device=dev)
 
-    # distinct pairs per rank (independent replicas)
-    host_pairs = [synth.paper_pair(pair_index=rank * args.pool + i) for i in range(args.pool)]
+    # B distinct pairs per rank (independent replicas); one step = one
+    # persistent launch over all B pairs
+    host_pairs = _pool_pairs(rank, B)
     dx = [torch.from_numpy(x).to(dev) for x, _ in host_pairs]
     dy = [torch.from_numpy(y).to(dev) for _, y in host_pairs]
-    lisi = [torch.empty(T * T, device=dev) for _ in range(args.pool)]
-    aug = [torch.empty(T * T, device=dev) for _ in range(args.pool)]
-    stream = torch.cuda.Stream(device=dev)
-    cfg = iqa.iqa_get_config(ctx, iqa.IQA_F32, N, NT, iqa.MAPS_BOTH).as_dict()
+    lisi = [torch.empty(T * T, device=dev) for _ in range(B)]
+    aug = [torch.empty(T * T, device=dev) for _ in range(B)]
 
-    def step(i, st):
-        j = i % args.pool
-        iqa.iqa_both(ctx, dx[j], dy[j], iqa.IQA_F32, N, NT, params, lisi[j], aug[j],
-                     None, st)
+    def make_plan(nt):
+        t = N // nt
+        lm = lisi if nt == NT else [torch.empty(t * t, device=dev) for _ in range(B)]
+        am = aug if nt == NT else [torch.empty(t * t, device=dev) for _ in range(B)]
+        pairs = [iqa.make_pair(dx[i], dy[i], N, nt, lm[i], am[i]) for i in range(B)]
+        return iqa.iqa_plan_create(ctx, pairs, iqa.IQA_F32, params, iqa.IQA_PLAN_GRAPH), (lm, am)
+
+    plan, _ = make_plan(NT)
+    tuned = iqa.iqa_plan_autotune(plan, stream, 3).as_dict()
+    info = iqa.iqa_plan_info(plan).as_dict()
 
     clocks = ClockSampler(local)
     clocks.start()
-    with torch.cuda.stream(stream):
-        for i in range(max(3, args.warmup)):
-            step(i, stream)
-    torch.cuda.synchronize()
-
-    # the timed K steps are replayed from a CUDA graph of G steps so that no
-    # host-side launch cost enters the device timing
     K = max(1, args.steps)
-    G = min(K, 10 * args.pool)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=stream):
-        for i in range(G):
-            step(i, stream)
-    tail = K % G
-    graph_tail = None
-    if tail:
-        graph_tail = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph_tail, stream=stream):
-            for i in range(tail):
-                step(i, stream)
-    torch.cuda.synchronize()
-
     barrier(world)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        e0.record(stream)
-        for _ in range(K // G):
-            graph.replay()
-        if graph_tail is not None:
-            graph_tail.replay()
-        e1.record(stream)
-    torch.cuda.synchronize()
+    dev_ms = _time_plan(iqa, ctx, plan, stream, K, args.warmup)
     barrier(world)
-    dev_ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     t_max_ms = max_over_ranks(dev_ms, world, dev)
 
-    # per-launch duration (events around single launches, a GPU-side delay
-    # ahead of each so the host call cost stays outside the events)
+    # one pair per launch (the plain call), back to back from a CUDA graph
+    G = 4 * B
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        for i in range(B):
+            iqa.iqa_both(ctx, dx[i], dy[i], iqa.IQA_F32, N, NT, params, lisi[i], aug[i],
+                         None, stream)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=stream):
+        for i in range(G):
+            j = i % B
+            iqa.iqa_both(ctx, dx[j], dy[j], iqa.IQA_F32, N, NT, params, lisi[j], aug[j],
+                         None, stream)
+    reps = max(1, min(50, K // G + 1))
+    with torch.cuda.stream(stream):
+        g.replay()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(reps):
+            g.replay()
+        p1.record(stream)
+    torch.cuda.synchronize()
+    per_pair_us = p0.elapsed_time(p1) * 1e3 / (reps * G)
     single = []
     for i in range(20):
         with torch.cuda.stream(stream):
@@ -295,11 +318,24 @@ def run_ours(args):
             a0 = torch.cuda.Event(enable_timing=True)
             a1 = torch.cuda.Event(enable_timing=True)
             a0.record(stream)
-            step(i + 3, stream)
+            iqa.iqa_both(ctx, dx[i % B], dy[i % B], iqa.IQA_F32, N, NT, params,
+                         lisi[i % B], aug[i % B], None, stream)
             a1.record(stream)
         torch.cuda.synchronize()
         single.append(a0.elapsed_time(a1) * 1e3)
     single_us = float(np.median(single[3:]))
+    plain_cfg = iqa.iqa_get_config(ctx, iqa.IQA_F32, N, NT, iqa.MAPS_BOTH).as_dict()
+
+    # N_T sweep of the batched form (the paper's Fig. 1 axis)
+    sweep = {}
+    for nt in PAPER_NT_SWEEP:
+        if nt == NT:
+            sweep[str(nt)] = round(K * B * pair_bytes / (dev_ms * 1e-3) / 1e9, 1)
+            continue
+        pl, _keep = make_plan(nt)
+        ms = _time_plan(iqa, ctx, pl, stream, max(10, min(K, 200)), 3)
+        sweep[str(nt)] = round(max(10, min(K, 200)) * B * pair_bytes / (ms * 1e-3) / 1e9, 1)
+        iqa.iqa_plan_destroy(pl)
 
     # end to end through the host-buffer entry point (page-locked buffers)
     hx = [torch.from_numpy(x).pin_memory() for x, _ in host_pairs[:4]]
@@ -307,20 +343,32 @@ def run_ours(args):
     hl = np.empty(T * T, np.float32)
     ha = np.empty(T * T, np.float32)
     for i in range(3):
-        iqa.iqa_both_host(ctx, hx[i % 4], hy[i % 4], iqa.IQA_F32, N, NT, params, hl, ha)
+        iqa.iqa_both_host(ctx, hx[i % len(hx)], hy[i % len(hy)], iqa.IQA_F32, N, NT, params,
+                          hl, ha)
     barrier(world)
     t0 = time.perf_counter()
     E = max(1, args.e2e_steps)
     for i in range(E):
-        iqa.iqa_both_host(ctx, hx[i % 4], hy[i % 4], iqa.IQA_F32, N, NT, params, hl, ha)
+        iqa.iqa_both_host(ctx, hx[i % len(hx)], hy[i % len(hy)], iqa.IQA_F32, N, NT, params,
+                          hl, ha)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     assert np.all(np.isfinite(hl)) and np.all(np.isfinite(ha))
+    # context for e2e: a plain page-locked host -> device copy of one pair
+    scratch = torch.empty(2 * N * N, device=dev)
+    hcat = torch.cat([hx[0].view(-1), hy[0].view(-1)]).pin_memory()
+    scratch.copy_(hcat, non_blocking=True)
+    torch.cuda.synchronize()
+    c0 = time.perf_counter()
+    for _ in range(10):
+        scratch.copy_(hcat, non_blocking=True)
+    torch.cuda.synchronize()
+    h2d_gbs = 10 * pair_bytes / (time.perf_counter() - c0) / 1e9
 
-    total_bytes = sum_over_ranks(K * pair_bytes, world, dev)
+    total_bytes = sum_over_ranks(K * B * pair_bytes, world, dev)
     value = total_bytes / (t_max_ms * 1e-3) / 1e9
     peak, peak_src = measured_peak()
     per_launch_us = dev_ms * 1e3 / K
-    achieved = pair_bytes / (per_launch_us * 1e-6) / 1e9
+    achieved = B * pair_bytes / (per_launch_us * 1e-6) / 1e9
     e2e_value = sum_over_ranks(E * pair_bytes, world, dev) / e2e_s / 1e9
 
     result = None
@@ -334,35 +382,44 @@ def run_ours(args):
             "ms_per_step": round(t_max_ms / K, 6), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded Gaussian-beam radio skies, no dataset)",
-            "config": {"workload": "paper-scale pair N=2048 N_T=64 FP32, LISI+augLISI "
-                                   "in one pass", "N": N, "N_T": NT, "tiles": T * T,
-                       "pool_pairs": args.pool,
-                       "l2": "inputs larger than L2: steps rotate over %d distinct pairs "
-                             "(%d MB)" % (args.pool, args.pool * pair_bytes // 2 ** 20),
-                       "params": PARAMS, "launch": cfg,
-                       "timing": "CUDA events around K steps replayed from a CUDA graph",
+            "config": {"workload": "paper-scale pairs N=2048 N_T=64 FP32, LISI+augLISI "
+                                   "in one pass, %d distinct pairs per step in one "
+                                   "persistent launch" % B,
+                       "N": N, "N_T": NT, "tiles_per_pair": T * T, "pairs_per_step": B,
+                       "l2": "inputs larger than L2: each step reads %d MB of distinct "
+                             "pairs" % (B * pair_bytes // 2 ** 20),
+                       "params": PARAMS, "launch": info["config"], "tuned": tuned,
+                       "timing": "CUDA events around K plan launches (graph replays)",
                        "parallelism": "replicas x%d" % world},
             "pct_of_peak": round(100 * value / world / peak, 2),
             "pairs_per_s": round(value * 1e9 / pair_bytes, 1),
             "pixel_pairs_per_s": round(value * 1e9 / 8, 1),
-            "kernel_us_per_pair": round(per_launch_us, 3),
-            "single_launch_us": round(single_us, 3),
+            "us_per_pair": round(per_launch_us / B, 3),
+            "one_pair_per_launch": {
+                "GBs": round(pair_bytes / (per_pair_us * 1e-6) / 1e9, 1),
+                "us_per_pair": round(per_pair_us, 3),
+                "single_launch_us": round(single_us, 3),
+                "launch": plain_cfg,
+                "timing": "back-to-back iqa_both launches replayed from a CUDA graph; "
+                          "single launch with a GPU-side delay queued ahead"},
+            "nt_sweep_GBs": sweep,
             "clocks": clk,
             "e2e": {"value": round(e2e_value, 2), "unit": "GB/s",
                     "h2d_bytes_per_step": pair_bytes,
                     "d2h_bytes_per_step": 2 * T * T * 4,
                     "ms_per_step": round(e2e_s * 1e3 / E, 4),
-                    "api": "iqa_both_host, page-locked host buffers"},
+                    "api": "iqa_both_host, one pair per call, page-locked host buffers",
+                    "plain_h2d_copy_GBs": round(h2d_gbs, 1)},
             "gpu_launches": K,
             "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": None, "peak_source": peak_src,
-                         "kernel": "iqa_tiles_kernel f32 threads=%d ilp=%d tiles_across=%d "
-                                   "split=%d" % (cfg["threads"], cfg["ilp"],
-                                                 cfg["tiles_across"], cfg["split"])},
+                         "kernel": "iqa_stream_kernel<float,%d,1,1> (persistent, TMA)"
+                                   % info["config"]["threads"]},
             "cpu_baseline": cpu,
             "paper_context": PAPER_H100,
         }
+    iqa.iqa_plan_destroy(plan)
     iqa.iqa_destroy(ctx)
     return result
 
