@@ -291,6 +291,38 @@ iqa_status iqa_plan_autotune(iqa_plan *plan, iqa_stream stream, int iters,
  */
 iqa_status iqa_wait(iqa_ctx *ctx, iqa_stream stream, int timeout_us);
 
+/*
+ * Batched launch for callers that cannot allocate device memory.  The paper
+ * has no counterpart to this entry point.
+ *
+ * Some callers must not call cudaMalloc once they are running: a real-time
+ * imaging pipeline that reserves all of the GPU's memory for its own buffers
+ * at start-up, or one that cannot afford the device-wide synchronisation an
+ * allocation may cause between observations.  This call computes the maps
+ * of up to IQA_NOALLOC_MAX_PAIRS pairs in one persistent launch, like a plan,
+ * but needs no context and allocates nothing: its work-list descriptors, work
+ * counter and status word live in one fixed array in device memory, declared
+ * in the library (about 25 KB), which every GPU that loads the library keeps
+ * until the process exits.  The caller passes the images and the outputs, as
+ * in iqa_pair.
+ *
+ * Set-up: the first call on each device looks up the array's device address
+ * (with that device current); make that first call before any stream capture.
+ * Every call copies its descriptors into the array and clears the counters on
+ * `stream`, then launches there, and returns without synchronising.  All calls
+ * share the one array, which keeps the last call's contents: calls whose work
+ * overlaps on the GPU (on different streams, or from different threads) race
+ * and give wrong maps, so order them on one stream or with events.  A device-
+ * side wait that runs out leaves maps unwritten and is not reported here (the
+ * plan path reports it through iqa_wait).
+ * Errors: IQA_ERR_INVALID_ARG (more than IQA_NOALLOC_MAX_PAIRS pairs, a bad
+ * pair, dtype or constants), IQA_ERR_UNSUPPORTED (a pair the TMA kernel cannot
+ * stream, as for iqa_plan_create), IQA_ERR_CUDA.  Reason: iqa_last_error(NULL).
+ */
+#define IQA_NOALLOC_MAX_PAIRS 64
+iqa_status iqa_batch_noalloc(const iqa_pair *pairs, int npairs, iqa_dtype dtype,
+                             const iqa_params *params, iqa_stream stream);
+
 /* Context options for iqa_set_option. */
 typedef enum {
     /* Bound, in microseconds, on every device-side wait of the persistent

@@ -83,6 +83,7 @@ class iqa_plan_stats(ctypes.Structure):
 
 
 IQA_PLAN_GRAPH = 1
+IQA_NOALLOC_MAX_PAIRS = 64
 IQA_OPT_WAIT_TIMEOUT_US = 1
 IQA_OPT_INJECT_STALL = 2
 
@@ -114,6 +115,7 @@ def _declare(lib):
         "iqa_plan_destroy": ([_vp], None),
         "iqa_plan_info": ([_vp, P(iqa_plan_stats)], _st),
         "iqa_plan_autotune": ([_vp, _vp, _i, P(iqa_launch_config)], _st),
+        "iqa_batch_noalloc": ([P(iqa_pair), _i, _i, P(iqa_params), _vp], _st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -298,3 +300,10 @@ def iqa_plan_autotune(plan, stream=None, iters=5):
     _check(plan.ctx, lib().iqa_plan_autotune(plan.handle, _stream(stream), int(iters),
                                              ctypes.byref(best)))
     return best
+
+
+def iqa_batch_noalloc(pairs, dtype, params=None, stream=None):
+    """Batched launch that allocates no device memory (see include/iqa.h)."""
+    arr = (iqa_pair * len(pairs))(*pairs)
+    return _check(None, lib().iqa_batch_noalloc(arr, len(pairs), int(dtype),
+                                                _params(params), _stream(stream)))

@@ -1,0 +1,102 @@
+"""iqa_batch_noalloc, the batched launch for callers that cannot allocate device
+memory (a pipeline that reserves all GPU memory at start-up, or that cannot
+afford an allocation's device-wide synchronisation mid-run), against the
+existing one-pair entry point iqa_both, through the C-ABI (needs a GPU).
+
+Collected last on purpose (file name), so that a run stopping at the first
+failure has run every other test before it; it also passes on its own in a
+fresh process.
+"""
+import numpy as np
+import pytest
+
+import parity
+from paper_2501_10653_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+PARAMS = {"C1": 1e-6, "C2": 1e-6, "C": 1e-6, "D": 0.0}
+
+
+@pytest.fixture(scope="module")
+def lib_ctx():
+    from paper_2501_10653_gb300 import build, iqa
+    build.build()
+    h = iqa.iqa_create(0, 0)
+    yield h
+    iqa.iqa_destroy(h)
+
+
+def _batch(specs, seed):
+    import torch
+    items = []
+    for i, (N, NT) in enumerate(specs):
+        x, y = synth.mixed_batch_pair(i, N, seed=seed)
+        T = N // NT
+        items.append(dict(N=N, NT=NT, dx=parity.to_device(x), dy=parity.to_device(y),
+                          l=torch.full((T * T,), float("nan"), device="cuda"),
+                          a=torch.full((T * T,), float("nan"), device="cuda"),
+                          s=torch.full((T * T, 4), float("nan"), device="cuda",
+                                       dtype=torch.float64)))
+    return items
+
+
+def _reference(ctx, it):
+    """The same pair through the existing entry point iqa_both."""
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    T = it["N"] // it["NT"]
+    l = torch.empty(T * T, device="cuda")
+    a = torch.empty(T * T, device="cuda")
+    s = torch.empty((T * T, 4), device="cuda", dtype=torch.float64)
+    iqa.iqa_both(ctx, it["dx"], it["dy"], iqa.IQA_F32, it["N"], it["NT"], PARAMS, l, a, s,
+                 torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    return l.cpu().numpy(), a.cpu().numpy(), s.cpu().numpy()
+
+
+def _check_against_reference(ctx, items):
+    for it in items:
+        want = _reference(ctx, it)
+        got = (it["l"].cpu().numpy(), it["a"].cpu().numpy(), it["s"].cpu().numpy())
+        parity.assert_parity(got, want, PARAMS)
+
+
+def test_noalloc_matches_existing_entry_point_on_two_calls_in_a_row(lib_ctx):
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    st = torch.cuda.current_stream()
+    first = _batch([(1024, 64), (512, 32), (256, 128), (768, 96)], seed=21)
+    second = _batch([(512, 128), (1024, 32), (256, 64)], seed=22)
+    pairs1 = [iqa.make_pair(it["dx"], it["dy"], it["N"], it["NT"], it["l"], it["a"], it["s"])
+              for it in first]
+    pairs2 = [iqa.make_pair(it["dx"], it["dy"], it["N"], it["NT"], it["l"], it["a"], it["s"])
+              for it in second]
+    iqa.iqa_batch_noalloc(pairs1, iqa.IQA_F32, PARAMS, st)
+    iqa.iqa_batch_noalloc(pairs2, iqa.IQA_F32, PARAMS, st)
+    torch.cuda.synchronize()
+    _check_against_reference(lib_ctx, first)
+    _check_against_reference(lib_ctx, second)
+    # the same pairs again: the shared array is reused, counters start at zero
+    for it in first:
+        it["l"].fill_(float("nan"))
+        it["a"].fill_(float("nan"))
+        it["s"].fill_(float("nan"))
+    iqa.iqa_batch_noalloc(pairs1, iqa.IQA_F32, PARAMS, st)
+    torch.cuda.synchronize()
+    _check_against_reference(lib_ctx, first)
+
+
+def test_noalloc_rejects_more_pairs_than_its_array_holds(lib_ctx):
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    d = torch.zeros(256 * 256, device="cuda")
+    m = torch.zeros(16, device="cuda")
+    p = iqa.make_pair(d, d, 256, 64, m)
+    with pytest.raises(iqa.IqaError) as ei:
+        iqa.iqa_batch_noalloc([p] * (iqa.IQA_NOALLOC_MAX_PAIRS + 1), iqa.IQA_F32, PARAMS,
+                              torch.cuda.current_stream())
+    assert ei.value.status == iqa.IQA_ERR_INVALID_ARG
+    assert "at most" in iqa.iqa_last_error(None)
+    torch.cuda.synchronize()
+    assert np.all(m.cpu().numpy() == 0)
