@@ -59,6 +59,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="bound on the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune-iters", type=int, default=3,
+                    help="launches per autotuner candidate (0: keep the default shape)")
     return ap.parse_args(argv)
 
 
@@ -275,7 +277,8 @@ def run_ours(args):
         return iqa.iqa_plan_create(ctx, pairs, iqa.IQA_F32, params, iqa.IQA_PLAN_GRAPH), (lm, am)
 
     plan, _ = make_plan(NT)
-    tuned = iqa.iqa_plan_autotune(plan, stream, 3).as_dict()
+    tuned = (iqa.iqa_plan_autotune(plan, stream, args.tune_iters).as_dict()
+             if args.tune_iters > 0 else None)
     info = iqa.iqa_plan_info(plan).as_dict()
 
     clocks = ClockSampler(local)

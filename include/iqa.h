@@ -172,8 +172,9 @@ iqa_status iqa_both_host(iqa_ctx *ctx, const void *hx, const void *hy,
  * `stage_kb` KB per image, and `threads` consumer threads reduce them.  Needs
  * 16-byte aligned images, NT a multiple of 16 bytes, tiles_across * NT <= 256.
  *   threads        128, 256 or 512 consumer threads (plus one producer warp)
- *   tiles_across   whole tiles per unit
- *   stages         2..16;   stage_kb  2, 4, 8 or 16;   ctas_per_sm  1 or 2
+ *   tiles_across   whole tiles per unit (plans choose it per pair from
+ *                  unit_kpx: the widest unit of at most unit_kpx K pixels)
+ *   stages         2..16;   stage_kb  2, 4, 8 or 16;   ctas_per_sm  1..4
  * maps: 1 = LISI only, 2 = augLISI only, 3 = both (also used when sums are
  * requested).  Unused fields are ignored.
  */
@@ -187,6 +188,7 @@ typedef struct {
     int stages;
     int stage_kb;
     int ctas_per_sm;
+    int unit_kpx;
 } iqa_launch_config;
 
 /*

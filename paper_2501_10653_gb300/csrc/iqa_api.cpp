@@ -405,6 +405,7 @@ iqa_status iqa_get_config(iqa_ctx *ctx, iqa_dtype dtype, int N, int NT, int maps
     out->stages = c.stages;
     out->stage_kb = c.stage_kb;
     out->ctas_per_sm = c.ctas_per_sm;
+    out->unit_kpx = c.unit_kpx;
     return IQA_OK;
 }
 
@@ -420,6 +421,7 @@ TileConfig from_public(const iqa_launch_config *cfg, iqa_dtype dtype)
     c.stages = cfg->stages;
     c.stage_kb = cfg->stage_kb;
     c.ctas_per_sm = cfg->ctas_per_sm;
+    c.unit_kpx = cfg->unit_kpx > 0 ? cfg->unit_kpx : 16;
     if (c.variant == 1) {
         c.S = 1;
         c.vec = 16 / elem_size(dtype);

@@ -38,22 +38,6 @@ struct iqa_plan {
 
 namespace iqa {
 
-// Widest unit (whole tiles, <= 256 elements, <= 16K pixels) whose row of
-// 16-byte vectors divides the consumer thread count.
-static int batch_tiles_across(int N, int NT, iqa_dtype dtype, int threads)
-{
-    const int V = 16 / elem_size(dtype);
-    const int T = N / NT;
-    int best = 1;
-    for (int tx = 2; tx <= kMaxTX && tx * NT <= 256; ++tx) {
-        if (T % tx) continue;
-        if ((long long)tx * NT * NT > 16384) break;
-        if (threads % (tx * NT / V)) continue;
-        best = tx;
-    }
-    return best;
-}
-
 static iqa_status check_pair(iqa_ctx *ctx, const iqa_pair &p, iqa_dtype dtype, int i)
 {
     if (!p.x || !p.y) {
@@ -86,7 +70,8 @@ static iqa_status plan_build(iqa_plan *pl, const TileConfig &cfg)
     for (int i = 0; i < n; ++i) {
         const iqa_pair &p = pl->pairs[i];
         TileConfig c = cfg;
-        c.TX = batch_tiles_across(p.N, p.NT, pl->dtype, cfg.threads);
+        c.TX = stream_tiles_across(p.N, p.NT, pl->dtype, cfg.threads,
+                                   (long long)cfg.unit_kpx * 1024);
         if (!stream_config_valid(p.N, p.NT, pl->dtype, c, &why)) {
             set_error(ctx, "pair %d (N=%d NT=%d): %s", i, p.N, p.NT, why.c_str());
             return IQA_ERR_INVALID_ARG;
@@ -293,6 +278,7 @@ iqa_status iqa_plan_info(const iqa_plan *plan, iqa_plan_stats *out)
     out->config.stages = plan->cfg.stages;
     out->config.stage_kb = plan->cfg.stage_kb;
     out->config.ctas_per_sm = plan->cfg.ctas_per_sm;
+    out->config.unit_kpx = plan->cfg.unit_kpx;
     return IQA_OK;
 }
 
@@ -307,9 +293,12 @@ iqa_status iqa_plan_autotune(iqa_plan *plan, iqa_stream stream, int iters,
     cudaEventCreate(&e1);
     float best_ms = 1e30f;
     TileConfig best = keep;
-    const int threads_c[] = {128, 256, 512};
-    const int shape_c[][3] = {{3, 16, 2}, {6, 8, 2}, {4, 16, 1}, {8, 8, 1},
-                              {12, 8, 1}, {5, 16, 1}, {2, 16, 2}, {4, 8, 2}};
+    const int threads_c[] = {128, 256};
+    // {stages, stage_kb, ctas_per_sm, unit_kpx}
+    const int shape_c[][4] = {{3, 16, 2, 16}, {2, 16, 2, 16}, {2, 16, 2, 4},
+                              {3, 16, 2, 4},  {6, 8, 2, 4},   {4, 8, 3, 4},
+                              {2, 16, 3, 4},  {4, 16, 1, 16}, {8, 8, 1, 4},
+                              {3, 8, 4, 4},   {2, 8, 4, 4},   {2, 16, 3, 16}};
     iqa_status s = IQA_OK;
     for (int th : threads_c) {
         for (const auto &sh : shape_c) {
@@ -318,6 +307,7 @@ iqa_status iqa_plan_autotune(iqa_plan *plan, iqa_stream stream, int iters,
             c.stages = sh[0];
             c.stage_kb = sh[1];
             c.ctas_per_sm = sh[2];
+            c.unit_kpx = sh[3];
             if (plan_build(plan, c) != IQA_OK) continue;
             cudaError_t e = plan_launch_direct(plan, (cudaStream_t)stream);  // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(e0, (cudaStream_t)stream);

@@ -148,11 +148,20 @@ __device__ __forceinline__ void unpack(const Raw<T, VEC> &r, float (&f)[VEC])
 }
 
 // ---------------------------------------------------------------------------
+// Approximate reciprocal: the PTX rcp.approx.f32 instruction (about one ulp
+// of error by the PTX ISA's bound; subnormals are not flushed).
+__device__ __forceinline__ float rcp_approx(float v)
+{
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
 // Per-pixel terms of Eq. 1 / Eq. 2 for VEC pixel pairs, summed pairwise.
 // Clamp: fmaxf(v, 0) returns 0 for v <= 0 and for NaN (the non-NaN operand).
-// With both pixels clamped, |x + y| = x + y.  The divide uses the fast
-// reciprocal-based __fdividef (<= 2 ulp for the denominators that occur here,
-// |x-y| + C1 in [C1, 2^126]).
+// With both pixels clamped, |x + y| = x + y.  The divide s / (d + C1) is
+// s * rcp(d + C1): the denominator is >= C1 > 0, and the product carries at
+// most about 2 ulp (the reciprocal's error plus one rounding).
 template <int VEC, bool DO_A, bool DO_B>
 __device__ __forceinline__ void pixel_terms(const float (&xv)[VEC],
                                             const float (&yv)[VEC], float C1f,
@@ -166,7 +175,7 @@ __device__ __forceinline__ void pixel_terms(const float (&xv)[VEC],
         float yc = fmaxf(yv[i], 0.0f);
         float s = xc + yc;
         float d = fabsf(xc - yc);
-        ta[i] = DO_A ? __fdividef(s, d + C1f) : 0.0f;
+        ta[i] = DO_A ? s * rcp_approx(d + C1f) : 0.0f;
         tb[i] = DO_B ? s * d : 0.0f;
         tx[i] = xc;
         ty[i] = yc;
@@ -268,21 +277,37 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
+// Barriers for reduce_unit: the whole CTA, or a named barrier over the
+// consumer warps of the persistent kernel (its producer warp does not take
+// part).
+struct CtaBarrier {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+template <int ID, int COUNT> struct NamedBarrier {
+    __device__ __forceinline__ void operator()() const
+    {
+        asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(COUNT) : "memory");
+    }
+};
+
+__device__ __forceinline__ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
 // Cross-thread reduction of one unit, in FP32 (the low-rate FP64 pipe of this
 // GPU is kept off the per-unit path).  part[tl * 4 + k] receives tile tl's sum
-// k (A, B, Sx, Sy).
+// k (A, B, Sx, Sy).  A thread's column is v % LPU and, for TX > 1, fixed
+// (the host guarantees THREADS % LPU == 0), so its tile is (tid % LPU) / LPT.
 //  * TX == 1: every warp reduces its lanes with an xor-shuffle tree, then warp
 //    0 combines the per-warp partials the same way.
-//  * TX > 1: the host guarantees THREADS % LPU == 0, so a thread's column and
-//    hence its tile is fixed; the threads of tile tl are q * LPU + tl * LPT + e
-//    (q < THREADS / LPU, e < LPT).  Their sums go through shared memory; warp
-//    w owns tiles w, w + warps, ... and sums its share lane-wise in a fixed
-//    order, then with a shuffle tree.
-template <int THREADS>
-__device__ __forceinline__ void reduce_unit(const float (&acc)[4], int TX,
-                                            int LPU, int LPT,
-                                            float (*red)[THREADS],
-                                            float *part)
+//  * TX > 1, LPT a power of two and the warp rows aligned (LPU >= 32, or LPU a
+//    power of two): a segmented shuffle tree sums each tile's LPT lanes (and,
+//    when a warp spans several unit rows, the same columns of those rows); the
+//    lane heading each segment stores one partial per (row group, tile); then
+//    thread tl sums tile tl's row-group partials in order.
+//  * otherwise: all four sums go through shared memory and warp w sums tiles
+//    w, w + warps, ... lane-wise in a fixed order, then with a shuffle tree.
+template <int THREADS, typename Bar>
+__device__ __forceinline__ void reduce_unit(const float (&acc)[4], int TX, int LPU, int LPT,
+                                            float (*red)[THREADS], float *part, Bar bar)
 {
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -293,7 +318,7 @@ __device__ __forceinline__ void reduce_unit(const float (&acc)[4], int TX,
             float v = warp_sum(acc[k]);
             if (lane == 0) red[k][warp] = v;
         }
-        __syncthreads();
+        bar();
         if (warp == 0) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -302,12 +327,43 @@ __device__ __forceinline__ void reduce_unit(const float (&acc)[4], int TX,
                 if (lane == 0) part[k] = v;
             }
         }
-        __syncthreads();
+        bar();
+        return;
+    }
+    if (is_pow2(LPT) && LPT <= 32 && (LPU >= 32 || is_pow2(LPU))) {
+        float v[4] = {acc[0], acc[1], acc[2], acc[3]};
+        for (int o = 1; o < LPT; o <<= 1) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        }
+        for (int o = LPU; o < 32; o <<= 1) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        }
+        const int span = LPU >= 32 ? LPU : 32;  // threads per row group
+        const int groups = THREADS / span;
+        const int col = tid % LPU;
+        if (col % LPT == 0 && (LPU >= 32 || lane < LPU)) {
+            const int slot = (tid / span) * TX + col / LPT;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) red[k][slot] = v[k];
+        }
+        bar();
+        for (int tl = tid; tl < TX; tl += THREADS) {
+            float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            for (int g = 0; g < groups; ++g) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) s[k] += red[k][g * TX + tl];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) part[tl * 4 + k] = s[k];
+        }
+        bar();
         return;
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) red[k][tid] = acc[k];
-    __syncthreads();
+    bar();
     const int count = (THREADS / LPU) * LPT;
     for (int tl = warp; tl < TX; tl += WARPS) {
         float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -319,11 +375,11 @@ __device__ __forceinline__ void reduce_unit(const float (&acc)[4], int TX,
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            float v = warp_sum(s[k]);
-            if (lane == 0) part[tl * 4 + k] = v;
+            float w = warp_sum(s[k]);
+            if (lane == 0) part[tl * 4 + k] = w;
         }
     }
-    __syncthreads();
+    bar();
 }
 
 // Eq. 1 / Eq. 2 per-tile combine and the output writes.  IEEE float division

@@ -22,6 +22,7 @@ struct TileConfig {
     int stages = 8;
     int stage_kb = 8;
     int ctas_per_sm = 1;
+    int unit_kpx = 16;  // variant 1, batched: target unit size in K pixel pairs
 };
 
 enum MapsMask { MAPS_A = 1, MAPS_B = 2, MAPS_AB = 3 };

@@ -128,13 +128,8 @@ extern "C" iqa_status iqa_batch_noalloc(const iqa_pair *pairs, int npairs, iqa_d
     for (int k = 0; k < npairs; ++k) {
         const iqa_pair &p = pairs[order[k]];
         TileConfig c = cfg;
-        c.TX = 1;
-        for (int tx = 2; tx <= kMaxTX && tx * p.NT <= 256; ++tx) {
-            if ((p.N / p.NT) % tx) continue;
-            if ((long long)tx * p.NT * p.NT > 16384) break;
-            if (cfg.threads % (tx * p.NT / V)) continue;
-            c.TX = tx;
-        }
+        c.TX = stream_tiles_across(p.N, p.NT, dtype, cfg.threads,
+                                   (long long)cfg.unit_kpx * 1024);
         std::string why;
         if (!stream_config_valid(p.N, p.NT, dtype, c, &why)) {
             set_error(nullptr, "pair %d: %s", order[k], why.c_str());

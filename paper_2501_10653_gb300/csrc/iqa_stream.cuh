@@ -155,56 +155,6 @@ __device__ __forceinline__ int find_pair(const PairDesc *d, int npairs, long lon
     return lo;
 }
 
-// Consumer-side reduction of one unit over the CT consumer threads, with
-// named barrier 1 (the producer warp does not take part).  Same order and
-// layout as reduce_unit in iqa_device.cuh.
-template <int CT>
-__device__ __forceinline__ void reduce_unit_consumers(const float (&acc)[4], int TX,
-                                                      int LPU, int LPT, float (*red)[CT],
-                                                      float *part)
-{
-    const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    constexpr int WARPS = CT / 32;
-    if (TX == 1) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float v = warp_sum(acc[k]);
-            if (lane == 0) red[k][warp] = v;
-        }
-        named_bar(1, CT);
-        if (warp == 0) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float v = lane < WARPS ? red[k][lane] : 0.0f;
-                v = warp_sum(v);
-                if (lane == 0) part[k] = v;
-            }
-        }
-        named_bar(1, CT);
-        return;
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) red[k][tid] = acc[k];
-    named_bar(1, CT);
-    const int count = (CT / LPU) * LPT;
-    for (int tl = warp; tl < TX; tl += WARPS) {
-        float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        for (int e = lane; e < count; e += 32) {
-            int q = e / LPT;
-            int src = q * LPU + tl * LPT + (e - q * LPT);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) s[k] += red[k][src];
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float v = warp_sum(s[k]);
-            if (lane == 0) part[tl * 4 + k] = v;
-        }
-    }
-    named_bar(1, CT);
-}
-
 __device__ __forceinline__ void write_tile_desc(const PairDesc &d, long long t, float A,
                                                 float B, float Sx, float Sy)
 {
@@ -339,7 +289,8 @@ __global__ void __launch_bounds__(CT + 32, 1)
     const int lane = tid & 31;
     const PairDesc *d = nullptr;
     long long u = -1, lu = 0;
-    int c = 0, V = 0;
+    int c = 0, V = 0, chunks = 0;
+    float C1f = 0.0f;
     Kahan ka, kb, kx, ky;
     for (long long k = 0;; ++k) {
         const int s = (int)(k % S);
@@ -350,11 +301,14 @@ __global__ void __launch_bounds__(CT + 32, 1)
         named_bar(2, CT);
         if (*((volatile int *)abort_flag)) return;
         if (c == 0) {
+            // a new unit: its descriptor fields are read once into registers
             u = stage_unit[s];
             if (u < 0) return;
             d = &descs[sp.npairs > 1 ? find_pair(descs, sp.npairs, u) : 0];
             lu = u - d->unit_begin;
             V = d->CH * d->LPU;
+            chunks = d->chunks;
+            C1f = d->C1f;
             ka = Kahan();
             kb = Kahan();
             kx = Kahan();
@@ -362,21 +316,33 @@ __global__ void __launch_bounds__(CT + 32, 1)
         }
         const uint4 *xs = reinterpret_cast<const uint4 *>(ring + (size_t)s * 2 * SB);
         const uint4 *ys = reinterpret_cast<const uint4 *>(ring + (size_t)s * 2 * SB + SB);
-        const float C1f = d->C1f;
         float ba = 0.0f, bb = 0.0f, bx = 0.0f, by = 0.0f;
-        for (int v = tid; v < V; v += CT) {
-            Raw<T, VEC> rx, ry;
-            rx.v = xs[v];
-            ry.v = ys[v];
-            float xv[VEC], yv[VEC];
-            unpack<T, VEC>(rx, xv);
-            unpack<T, VEC>(ry, yv);
-            float a, b, sx, sy;
-            pixel_terms<VEC, DO_A, DO_B>(xv, yv, C1f, a, b, sx, sy);
-            ba += a;
-            bb += b;
-            bx += sx;
-            by += sy;
+        // four vectors of each image per thread per pass, loaded together
+        for (int v0 = tid; v0 < V; v0 += 4 * CT) {
+            Raw<T, VEC> rx[4], ry[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int v = v0 + j * CT;
+                if (v < V) {
+                    rx[j].v = xs[v];
+                    ry[j].v = ys[v];
+                } else {
+                    rx[j] = zero_raw<T, VEC>();
+                    ry[j] = zero_raw<T, VEC>();
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float xv[VEC], yv[VEC];
+                unpack<T, VEC>(rx[j], xv);
+                unpack<T, VEC>(ry[j], yv);
+                float a, b, sx, sy;
+                pixel_terms<VEC, DO_A, DO_B>(xv, yv, C1f, a, b, sx, sy);
+                ba += a;
+                bb += b;
+                bx += sx;
+                by += sy;
+            }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
@@ -384,14 +350,15 @@ __global__ void __launch_bounds__(CT + 32, 1)
         if (DO_B) kb.add(bb);
         kx.add(bx);
         ky.add(by);
-        if (++c == d->chunks) {
+        if (++c == chunks) {
             c = 0;
+            const int TX = d->TX, LPU = d->LPU, LPT = d->LPT;
             float acc[4] = {ka.value(), kb.value(), kx.value(), ky.value()};
-            reduce_unit_consumers<CT>(acc, d->TX, d->LPU, d->LPT, red, part);
+            reduce_unit<CT>(acc, TX, LPU, LPT, red, part, NamedBarrier<1, CT>());
             const int trow = (int)(lu / d->units_x);
             const int ucol = (int)(lu - (long long)trow * d->units_x);
-            const long long t0 = (long long)trow * d->T + (long long)ucol * d->TX;
-            for (int tl = tid; tl < d->TX; tl += CT)
+            const long long t0 = (long long)trow * d->T + (long long)ucol * TX;
+            for (int tl = tid; tl < TX; tl += CT)
                 write_tile_desc(*d, t0 + tl, part[tl * 4 + 0], part[tl * 4 + 1],
                                 part[tl * 4 + 2], part[tl * 4 + 3]);
         }

@@ -68,7 +68,7 @@ bool stream_config_valid(int N, int NT, iqa_dtype dtype, const TileConfig &c,
     if (c.stages < 2 || c.stages > 16) return fail("stages must be 2..16");
     if (c.stage_kb != 2 && c.stage_kb != 4 && c.stage_kb != 8 && c.stage_kb != 16)
         return fail("stage_kb must be 2, 4, 8 or 16");
-    if (c.ctas_per_sm != 1 && c.ctas_per_sm != 2) return fail("ctas_per_sm must be 1 or 2");
+    if (c.ctas_per_sm < 1 || c.ctas_per_sm > 4) return fail("ctas_per_sm must be 1..4");
     if (NT % V) return fail("the TMA kernel needs NT to be a multiple of 16 bytes");
     const int T = N / NT;
     if (c.TX < 1 || c.TX > kMaxTX || T % c.TX) return fail("tiles_across must divide N/NT");
@@ -78,10 +78,26 @@ bool stream_config_valid(int N, int NT, iqa_dtype dtype, const TileConfig &c,
     if (c.TX > 1 && c.threads % LPU) return fail("threads must be a multiple of the unit row");
     if (!chunk_rows(NT, BW, es, c.stage_kb * 1024))
         return fail("a unit row does not fit one stage");
-    if (stream_smem_bytes(c.stages, c.stage_kb * 1024, c.threads) * c.ctas_per_sm >
-        (size_t)227 * 1024)
+    if ((stream_smem_bytes(c.stages, c.stage_kb * 1024, c.threads) + 1024) * c.ctas_per_sm >
+        (size_t)228 * 1024)
         return fail("stages * stage_kb exceed shared memory");
     return true;
+}
+
+// Widest unit (whole tiles, <= 256 elements across, <= unit_px pixel pairs)
+// whose row of 16-byte vectors divides the consumer thread count.
+int stream_tiles_across(int N, int NT, iqa_dtype dtype, int threads, long long unit_px)
+{
+    const int V = 16 / elem_size(dtype);
+    const int T = N / NT;
+    int best = 1;
+    for (int tx = 2; tx <= kMaxTX && tx * NT <= 256; ++tx) {
+        if (T % tx) continue;
+        if ((long long)tx * NT * NT > unit_px) break;
+        if (threads % (tx * NT / V)) continue;
+        best = tx;
+    }
+    return best;
 }
 
 TileConfig default_stream_config(int N, int NT, iqa_dtype dtype)
@@ -92,19 +108,7 @@ TileConfig default_stream_config(int N, int NT, iqa_dtype dtype)
     c.stages = 8;
     c.stage_kb = 8;
     c.ctas_per_sm = 1;
-    const int es = elem_size(dtype);
-    const int V = 16 / es;
-    const int T = N / NT;
-    // widest unit up to 256 elements whose row divides the consumer count
-    int best = 1;
-    for (int tx = 2; tx <= kMaxTX && tx * NT <= 256; ++tx) {
-        if (T % tx) continue;
-        if ((long long)tx * NT * NT > 16384) break;
-        int lpu = tx * NT / V;
-        if (c.threads % lpu) continue;
-        best = tx;
-    }
-    c.TX = best;
+    c.TX = stream_tiles_across(N, NT, dtype, c.threads, 16384);
     return c;
 }
 

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(THREADS)
     float acc[4];
     accumulate_unit<T, VEC, ILP, THREADS, DO_A, DO_B>(xu, yu, p.N, p.RH, p.LPU,
                                                       p.C1f, acc);
-    reduce_unit<THREADS>(acc, p.TX, p.LPU, p.LPT, red, part);
+    reduce_unit<THREADS>(acc, p.TX, p.LPU, p.LPT, red, part, CtaBarrier());
 
     const long long t0 = (long long)tile_row * p.T + tile_col0;
     if (p.S == 1) {

@@ -59,7 +59,7 @@ class iqa_launch_config(ctypes.Structure):
                 ("ilp", ctypes.c_int), ("tiles_across", ctypes.c_int),
                 ("split", ctypes.c_int), ("vector", ctypes.c_int),
                 ("stages", ctypes.c_int), ("stage_kb", ctypes.c_int),
-                ("ctas_per_sm", ctypes.c_int)]
+                ("ctas_per_sm", ctypes.c_int), ("unit_kpx", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -238,7 +238,7 @@ def iqa_set_config(ctx, dtype, N, NT, maps, cfg):
         if isinstance(cfg, dict):
             full = {"variant": 0, "threads": 256, "ilp": 4, "tiles_across": 1,
                     "split": 1, "vector": 1, "stages": 8, "stage_kb": 8,
-                    "ctas_per_sm": 1}
+                    "ctas_per_sm": 1, "unit_kpx": 16}
             full.update(cfg)
             cfg = iqa_launch_config(**full)
         ref = ctypes.byref(cfg)
