@@ -132,23 +132,43 @@ iqa_status iqa_both(iqa_ctx *ctx, const void *x, const void *y, iqa_dtype dtype,
                     float *aug_map, double *sums, iqa_stream stream);
 
 /*
- * End-to-end form of iqa_both for images in HOST memory (Section 2's
- * interface: images in, IQA matrix out).  The context copies the images to
- * its device workspace in row bands on one of its own streams and computes
- * each band as soon as it lands, so copies and kernels overlap; the maps (and
- * sums) are copied back to host memory.  Page-locked host buffers give full
- * copy bandwidth; pageable ones work but are slower.  Synchronous: returns
- * when the host outputs are written.
+ * End-to-end form of iqa_both for images in HOST memory (Section 2's host
+ * interface: images in, IQA matrix out).  The context uploads x and y to its
+ * device workspace on one of its own streams, reduces them on another, and
+ * copies the maps (and sums) back to host memory.  Page-locked host buffers
+ * give full copy bandwidth; pageable ones work but are slower.  Synchronous:
+ * returns when the host outputs are written.
  *   hx, hy               host pointers, N*N elements of dtype
  *   lisi_map, aug_map    host pointers, (N/NT)^2 float32 each, either NULL
  *   sums                 host pointer or NULL, (N/NT)^2 x 4 float64
- * Errors: as iqa_both, plus IQA_ERR_NOMEM when 2*N*N elements of workspace do
- * not fit the context's HBM budget.
+ * Errors: as iqa_both, plus IQA_ERR_NOMEM when the workspace (both images,
+ * maps and sums of the pair) does not fit the context's HBM budget.
  */
 iqa_status iqa_both_host(iqa_ctx *ctx, const void *hx, const void *hy,
                          iqa_dtype dtype, int N, int NT,
                          const iqa_params *params, float *lisi_map,
                          float *aug_map, double *sums);
+
+/* One pair of host buffers for iqa_both_host_many (fields as iqa_both_host). */
+typedef struct {
+    const void *hx;
+    const void *hy;
+    int N;
+    int NT;
+    float *lisi_map;
+    float *aug_map;
+    double *sums;
+} iqa_host_pair;
+
+/*
+ * iqa_both_host over a sequence of pairs (any mix of N and N_T, one dtype),
+ * pipelined: two device slots, so the upload of pair k+1 overlaps the
+ * reduction and read-back of pair k and the host-to-device link stays busy.
+ * Synchronous: returns when every pair's host outputs are written.
+ * Errors: as iqa_both_host (the workspace is two slots of the largest pair).
+ */
+iqa_status iqa_both_host_many(iqa_ctx *ctx, const iqa_host_pair *pairs, int npairs,
+                              iqa_dtype dtype, const iqa_params *params);
 
 /*
  * Launch shape for one (dtype, N, NT, maps) key.  The paper gives each tile
@@ -207,6 +227,26 @@ iqa_status iqa_get_config(iqa_ctx *ctx, iqa_dtype dtype, int N, int NT, int maps
  */
 iqa_status iqa_set_config(iqa_ctx *ctx, iqa_dtype dtype, int N, int NT, int maps,
                           const iqa_launch_config *cfg);
+
+/*
+ * Eq. 3 and Eq. 4 (Section 3): the LISI and augLISI of larger tiles made by
+ * merging every m x m block of tiles -- with m = T the whole image -- from the
+ * per-tile sums of a previous map call, without re-reading any pixel.  Eq. 3
+ * weights lisi_t by max(Sx_t, Sy_t) + C2 (= D A_t by Eq. 1) and Eq. 4 weights
+ * auglisi_t by Sx_t + Sy_t + C (= Sx_t + Sy_t + C - B_t by Eq. 2), so both
+ * equal Eq. 1 / Eq. 2 on the block's summed (A, B, Sx, Sy); the kernel forms
+ * those sums in FP64 and applies the equations once per merged tile.
+ *   sums          device (T*T) x 4 float64 (A, B, Sx, Sy), T = N/N_T, tile
+ *                 t = r*T + c, as written by iqa_lisi / iqa_auglisi / iqa_both
+ *   m             merge factor, divides T
+ *   params        the constants used for the tiles (NULL = defaults)
+ *   merged_lisi, merged_aug   device (T/m)^2 float32, row-major, or NULL
+ *   merged_sums   device (T/m)^2 x 4 float64, or NULL
+ * Stream-ordered.  Errors: IQA_ERR_INVALID_ARG, IQA_ERR_CUDA.
+ */
+iqa_status iqa_merge(iqa_ctx *ctx, const double *sums, int T, int m,
+                     const iqa_params *params, float *merged_lisi, float *merged_aug,
+                     double *merged_sums, iqa_stream stream);
 
 /* ---------------------------------------------------------------------------
  * Batched form: many pairs, one persistent launch.

@@ -342,6 +342,7 @@ void iqa_destroy(iqa_ctx *ctx)
     if (ctx->s_comp) cudaStreamSynchronize(ctx->s_comp);
     for (cudaEvent_t ev : ctx->band_events) cudaEventDestroy(ev);
     if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->s_copy) cudaStreamDestroy(ctx->s_copy);
     if (ctx->s_comp) cudaStreamDestroy(ctx->s_comp);

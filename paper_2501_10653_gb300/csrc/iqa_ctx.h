@@ -42,6 +42,10 @@ struct iqa_ctx {
     cudaStream_t s_copy = nullptr;
     cudaStream_t s_comp = nullptr;
     std::vector<cudaEvent_t> band_events;
+    // page-locked staging for read-backs, so a pageable destination does not
+    // block the host thread between pairs
+    void *h_stage = nullptr;
+    size_t h_stage_bytes = 0;
 };
 
 namespace iqa {

@@ -1,10 +1,13 @@
-// iqa_host.cpp -- iqa_both_host: images in host memory, maps back in host
-// memory (the paper's host interface, Section 2), with the upload of each row
-// band overlapped with the kernel of the band before it.
+// iqa_host.cpp -- the end-to-end path from host memory: images in, IQA maps
+// out (the paper's host interface, Section 2).  iqa_both_host_many streams a
+// sequence of pairs through two device slots: the upload of pair k+1 (copy
+// stream) runs while pair k is reduced and its maps are read back (compute
+// stream), so the host-to-device link stays busy.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 
 #include "iqa.h"
 #include "iqa_ctx.h"
@@ -41,75 +44,91 @@ iqa_status ensure_workspace(iqa_ctx *ctx, size_t need)
     return IQA_OK;
 }
 
+// Grows the page-locked read-back staging to `need` bytes.
+iqa_status ensure_stage(iqa_ctx *ctx, size_t need)
+{
+    if (ctx->h_stage_bytes >= need) return IQA_OK;
+    if (ctx->h_stage) {
+        cudaFreeHost(ctx->h_stage);
+        ctx->h_stage = nullptr;
+        ctx->h_stage_bytes = 0;
+    }
+    cudaError_t e = cudaMallocHost(&ctx->h_stage, need);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(ctx, "page-locked staging of %zu bytes failed: %s", need,
+                  cudaGetErrorString(e));
+        return IQA_ERR_NOMEM;
+    }
+    ctx->h_stage_bytes = need;
+    return IQA_OK;
+}
+
+struct SlotLayout {
+    size_t off_y, off_l, off_a, off_s, bytes;
+};
+
+SlotLayout slot_layout(size_t img_bytes, size_t n_tiles)
+{
+    SlotLayout L;
+    L.off_y = round_up(img_bytes, 256);
+    L.off_l = L.off_y + round_up(img_bytes, 256);
+    L.off_a = L.off_l + round_up(n_tiles * 4, 256);
+    L.off_s = L.off_a + round_up(n_tiles * 4, 256);
+    L.bytes = L.off_s + round_up(n_tiles * 32, 256);
+    return L;
+}
+
 }  // namespace
 
-extern "C" iqa_status iqa_both_host(iqa_ctx *ctx, const void *hx, const void *hy,
-                                    iqa_dtype dtype, int N, int NT,
-                                    const iqa_params *params, float *lisi_map,
-                                    float *aug_map, double *sums)
+extern "C" iqa_status iqa_both_host_many(iqa_ctx *ctx, const iqa_host_pair *pairs, int npairs,
+                                         iqa_dtype dtype, const iqa_params *params)
 {
     if (!ctx) return IQA_ERR_INVALID_ARG;
-    if (!hx || !hy) {
-        set_error(ctx, "hx and hy must be host pointers, got NULL");
-        return IQA_ERR_INVALID_ARG;
-    }
-    if (!lisi_map && !aug_map && !sums) {
-        set_error(ctx, "no output requested");
+    if (!pairs || npairs < 1) {
+        set_error(ctx, "need pairs and npairs >= 1");
         return IQA_ERR_INVALID_ARG;
     }
     if (!dtype_ok(dtype)) {
         set_error(ctx, "unknown dtype %d", (int)dtype);
         return IQA_ERR_INVALID_ARG;
     }
-    iqa_status s = check_shape(ctx, N, NT);
-    if (s != IQA_OK) return s;
     iqa_params P;
-    s = resolve_params(ctx, params, &P);
+    iqa_status s = resolve_params(ctx, params, &P);
     if (s != IQA_OK) return s;
+    size_t max_img = 0, max_tiles = 0, out_bytes = 0;
+    for (int i = 0; i < npairs; ++i) {
+        const iqa_host_pair &p = pairs[i];
+        if (!p.hx || !p.hy) {
+            set_error(ctx, "pair %d: hx and hy must be host pointers, got NULL", i);
+            return IQA_ERR_INVALID_ARG;
+        }
+        if (!p.lisi_map && !p.aug_map && !p.sums) {
+            set_error(ctx, "pair %d: no output requested", i);
+            return IQA_ERR_INVALID_ARG;
+        }
+        s = check_shape(ctx, p.N, p.NT);
+        if (s != IQA_OK) return s;
+        const size_t T = p.N / p.NT;
+        max_img = std::max(max_img, (size_t)p.N * p.N * elem_size(dtype));
+        max_tiles = std::max(max_tiles, T * T);
+        out_bytes += T * T * 40;
+    }
 
     std::lock_guard<std::mutex> guard(ctx->host_mu);
     int prev = 0;
     cudaGetDevice(&prev);
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
-
-    const int T = N / NT;
-    const size_t n = (size_t)T * T;
-    const size_t img = (size_t)N * N * elem_size(dtype);
-    const size_t off_y = round_up(img, 256);
-    const size_t off_l = off_y + round_up(img, 256);
-    const size_t off_a = off_l + round_up(n * 4, 256);
-    const size_t off_s = off_a + round_up(n * 4, 256);
-    const size_t need = off_s + round_up(n * 32, 256);
-    s = ensure_workspace(ctx, need);
+    const SlotLayout L = slot_layout(max_img, max_tiles);
+    const int slots = npairs > 1 ? 2 : 1;
+    s = ensure_workspace(ctx, L.bytes * slots);
+    if (s == IQA_OK) s = ensure_stage(ctx, out_bytes);
     if (s != IQA_OK) {
         cudaSetDevice(prev);
         return s;
     }
-    char *ws = static_cast<char *>(ctx->ws);
-    void *dx = ws, *dy = ws + off_y;
-    float *dl = lisi_map ? reinterpret_cast<float *>(ws + off_l) : nullptr;
-    float *da = aug_map ? reinterpret_cast<float *>(ws + off_a) : nullptr;
-    double *dsm = sums ? reinterpret_cast<double *>(ws + off_s) : nullptr;
-
-    const int maps = sums ? MAPS_AB : ((dl ? MAPS_A : 0) | (da ? MAPS_B : 0));
-    TileConfig c = pick_config(ctx, N, NT, dtype, maps, true);
-    std::string why;
-    if (!config_valid(N, NT, dtype, c, &why)) {
-        cudaSetDevice(prev);
-        set_error(ctx, "no launch shape for N=%d NT=%d: %s", N, NT, why.c_str());
-        return IQA_ERR_UNSUPPORTED;
-    }
-    TileArgs a = make_args(dx, dy, N, NT, c, P, dl, da, dsm);
-
-    // Row bands of whole tile rows: about 4 MB of each image per band, at most
-    // 16 bands.  Band b's upload runs on s_copy while band b-1 computes on
-    // s_comp.
-    const size_t row_bytes = (size_t)NT * N * elem_size(dtype);
-    int rows_per_band = (int)std::max<size_t>(1, (4u << 20) / std::max<size_t>(1, row_bytes));
-    rows_per_band = std::max(rows_per_band, (T + 15) / 16);
-    const int bands = (T + rows_per_band - 1) / rows_per_band;
-    while ((int)ctx->band_events.size() < bands) {
+    while (ctx->band_events.size() < 4) {
         cudaEvent_t ev;
         e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         if (e != cudaSuccess) {
@@ -118,36 +137,91 @@ extern "C" iqa_status iqa_both_host(iqa_ctx *ctx, const void *hx, const void *hy
         }
         ctx->band_events.push_back(ev);
     }
-    for (int b = 0; b < bands && e == cudaSuccess; ++b) {
-        const int r0 = b * rows_per_band;
-        const int r1 = std::min(T, r0 + rows_per_band);
-        const size_t off = (size_t)r0 * row_bytes;
-        const size_t len = (size_t)(r1 - r0) * row_bytes;
-        e = cudaMemcpyAsync(static_cast<char *>(dx) + off,
-                            static_cast<const char *>(hx) + off, len,
-                            cudaMemcpyHostToDevice, ctx->s_copy);
+    cudaEvent_t *loaded = &ctx->band_events[0];  // per slot: images on the device
+    cudaEvent_t *done = &ctx->band_events[2];    // per slot: slot free again
+    char *stage = static_cast<char *>(ctx->h_stage);
+    size_t stage_off = 0;
+    for (int i = 0; i < npairs && e == cudaSuccess && s == IQA_OK; ++i) {
+        const iqa_host_pair &p = pairs[i];
+        const int slot = i % slots;
+        char *base = static_cast<char *>(ctx->ws) + (size_t)slot * L.bytes;
+        const size_t img = (size_t)p.N * p.N * elem_size(dtype);
+        const size_t n = (size_t)(p.N / p.NT) * (p.N / p.NT);
+        float *dl = p.lisi_map ? reinterpret_cast<float *>(base + L.off_l) : nullptr;
+        float *da = p.aug_map ? reinterpret_cast<float *>(base + L.off_a) : nullptr;
+        double *dsm = p.sums ? reinterpret_cast<double *>(base + L.off_s) : nullptr;
+        // the slot's previous pair must have been reduced and read back
+        if (i >= slots) e = cudaStreamWaitEvent(ctx->s_copy, done[slot], 0);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(static_cast<char *>(dy) + off,
-                                static_cast<const char *>(hy) + off, len,
-                                cudaMemcpyHostToDevice, ctx->s_copy);
-        if (e == cudaSuccess) e = cudaEventRecord(ctx->band_events[b], ctx->s_copy);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_comp, ctx->band_events[b], 0);
-        if (e == cudaSuccess) {
-            a.tile_row0 = r0;
-            e = launch_tiles(a, c, dtype, maps, r1 - r0, ctx->s_comp);
+            e = cudaMemcpyAsync(base, p.hx, img, cudaMemcpyHostToDevice, ctx->s_copy);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(base + L.off_y, p.hy, img, cudaMemcpyHostToDevice,
+                                ctx->s_copy);
+        if (e == cudaSuccess) e = cudaEventRecord(loaded[slot], ctx->s_copy);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_comp, loaded[slot], 0);
+        if (e != cudaSuccess) break;
+        const int maps = dsm ? MAPS_AB : ((dl ? MAPS_A : 0) | (da ? MAPS_B : 0));
+        TileConfig c = pick_config(ctx, p.N, p.NT, dtype, maps, true);
+        std::string why;
+        if (!any_config_valid(p.N, p.NT, dtype, c, &why)) {
+            set_error(ctx, "no launch shape for N=%d NT=%d: %s", p.N, p.NT, why.c_str());
+            s = IQA_ERR_UNSUPPORTED;
+            break;
         }
+        if (c.variant == 1) {
+            s = run_stream_pair(ctx, base, base + L.off_y, dtype, p.N, p.NT, c, P, dl, da,
+                                dsm, maps, ctx->s_comp);
+        } else {
+            TileArgs a = make_args(base, base + L.off_y, p.N, p.NT, c, P, dl, da, dsm);
+            e = launch_tiles(a, c, dtype, maps, p.N / p.NT, ctx->s_comp);
+        }
+        // maps go to page-locked staging (copied out after the last pair)
+        if (e == cudaSuccess && s == IQA_OK && p.lisi_map)
+            e = cudaMemcpyAsync(stage + stage_off, dl, n * 4, cudaMemcpyDeviceToHost,
+                                ctx->s_comp);
+        if (e == cudaSuccess && s == IQA_OK && p.aug_map)
+            e = cudaMemcpyAsync(stage + stage_off + n * 4, da, n * 4, cudaMemcpyDeviceToHost,
+                                ctx->s_comp);
+        if (e == cudaSuccess && s == IQA_OK && p.sums)
+            e = cudaMemcpyAsync(stage + stage_off + n * 8, dsm, n * 32,
+                                cudaMemcpyDeviceToHost, ctx->s_comp);
+        stage_off += n * 40;
+        if (e == cudaSuccess && s == IQA_OK) e = cudaEventRecord(done[slot], ctx->s_comp);
     }
-    if (e == cudaSuccess && lisi_map)
-        e = cudaMemcpyAsync(lisi_map, dl, n * 4, cudaMemcpyDeviceToHost, ctx->s_comp);
-    if (e == cudaSuccess && aug_map)
-        e = cudaMemcpyAsync(aug_map, da, n * 4, cudaMemcpyDeviceToHost, ctx->s_comp);
-    if (e == cudaSuccess && sums)
-        e = cudaMemcpyAsync(sums, dsm, n * 32, cudaMemcpyDeviceToHost, ctx->s_comp);
     cudaError_t e2 = cudaStreamSynchronize(ctx->s_comp);
     cudaError_t e3 = cudaStreamSynchronize(ctx->s_copy);
+    if (s == IQA_OK && e == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess) {
+        stage_off = 0;
+        for (int i = 0; i < npairs; ++i) {
+            const iqa_host_pair &p = pairs[i];
+            const size_t n = (size_t)(p.N / p.NT) * (p.N / p.NT);
+            if (p.lisi_map) std::memcpy(p.lisi_map, stage + stage_off, n * 4);
+            if (p.aug_map) std::memcpy(p.aug_map, stage + stage_off + n * 4, n * 4);
+            if (p.sums) std::memcpy(p.sums, stage + stage_off + n * 8, n * 32);
+            stage_off += n * 40;
+        }
+    }
     cudaSetDevice(prev);
+    if (s != IQA_OK) return s;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "host-path enqueue");
     if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "host-path compute stream");
     if (e3 != cudaSuccess) return cuda_fail(ctx, e3, "host-path copy stream");
     return IQA_OK;
+}
+
+extern "C" iqa_status iqa_both_host(iqa_ctx *ctx, const void *hx, const void *hy,
+                                    iqa_dtype dtype, int N, int NT,
+                                    const iqa_params *params, float *lisi_map,
+                                    float *aug_map, double *sums)
+{
+    if (!ctx) return IQA_ERR_INVALID_ARG;
+    iqa_host_pair p;
+    p.hx = hx;
+    p.hy = hy;
+    p.N = N;
+    p.NT = NT;
+    p.lisi_map = lisi_map;
+    p.aug_map = aug_map;
+    p.sums = sums;
+    return iqa_both_host_many(ctx, &p, 1, dtype, params);
 }

@@ -71,6 +71,12 @@ class iqa_pair(ctypes.Structure):
                 ("aug_map", ctypes.c_void_p), ("sums", ctypes.c_void_p)]
 
 
+class iqa_host_pair(ctypes.Structure):
+    _fields_ = [("hx", ctypes.c_void_p), ("hy", ctypes.c_void_p), ("N", ctypes.c_int),
+                ("NT", ctypes.c_int), ("lisi_map", ctypes.c_void_p),
+                ("aug_map", ctypes.c_void_p), ("sums", ctypes.c_void_p)]
+
+
 class iqa_plan_stats(ctypes.Structure):
     _fields_ = [("npairs", ctypes.c_int), ("total_units", ctypes.c_longlong),
                 ("grid", ctypes.c_int), ("input_bytes", ctypes.c_ulonglong),
@@ -116,6 +122,8 @@ def _declare(lib):
         "iqa_plan_info": ([_vp, P(iqa_plan_stats)], _st),
         "iqa_plan_autotune": ([_vp, _vp, _i, P(iqa_launch_config)], _st),
         "iqa_batch_noalloc": ([P(iqa_pair), _i, _i, P(iqa_params), _vp], _st),
+        "iqa_merge": ([_vp, _vp, _i, _i, P(iqa_params), _vp, _vp, _vp, _vp], _st),
+        "iqa_both_host_many": ([_vp, P(iqa_host_pair), _i, _i, P(iqa_params)], _st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -307,3 +315,21 @@ def iqa_batch_noalloc(pairs, dtype, params=None, stream=None):
     arr = (iqa_pair * len(pairs))(*pairs)
     return _check(None, lib().iqa_batch_noalloc(arr, len(pairs), int(dtype),
                                                 _params(params), _stream(stream)))
+
+
+def iqa_merge(ctx, sums, T, m, params, merged_lisi, merged_aug, merged_sums=None,
+              stream=None):
+    return _check(ctx, lib().iqa_merge(ctx, _ptr(sums), int(T), int(m), _params(params),
+                                       _ptr(merged_lisi), _ptr(merged_aug),
+                                       _ptr(merged_sums), _stream(stream)))
+
+
+def make_host_pair(hx, hy, N, NT, lisi_map=None, aug_map=None, sums=None):
+    return iqa_host_pair(_ptr(hx), _ptr(hy), int(N), int(NT), _ptr(lisi_map),
+                         _ptr(aug_map), _ptr(sums))
+
+
+def iqa_both_host_many(ctx, pairs, dtype, params=None):
+    arr = (iqa_host_pair * len(pairs))(*pairs)
+    return _check(ctx, lib().iqa_both_host_many(ctx, arr, len(pairs), int(dtype),
+                                                _params(params)))

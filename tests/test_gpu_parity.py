@@ -315,3 +315,68 @@ def test_tma_kernel_single_maps(ctx, orc, paper, which):
     got = parity.gpu_maps(ctx, x, y, 64, PARAMS, which)
     iqa.iqa_set_config(ctx, iqa.IQA_F32, 2048, 64, maps, None)
     parity.assert_parity(got, want, PARAMS)
+
+
+@pytest.mark.parametrize("NT,m", [(16, 2), (16, 8), (32, 4), (64, 32), (64, 1), (128, 16)])
+def test_merge_eq3_eq4_against_oracle(ctx, orc, paper, NT, m):
+    """Eq. 3 / Eq. 4 merging of m x m tile blocks (m = T: the whole image) from
+    the GPU's per-tile sums, against the oracle's merge (Eq. 3 / Eq. 4 in the
+    paper's form) and against the oracle computed directly at N_T' = m N_T."""
+    import torch
+    import oracle
+    from paper_2501_10653_gb300 import iqa
+    x, y = paper
+    N = 2048
+    T = N // NT
+    M = T // m
+    _, _, sums = parity.gpu_maps(ctx, x, y, NT, PARAMS)
+    ds = torch.from_numpy(sums).cuda()
+    ml = torch.full((M * M,), float("nan"), device="cuda")
+    ma = torch.full((M * M,), float("nan"), device="cuda")
+    msum = torch.full((M * M, 4), float("nan"), device="cuda", dtype=torch.float64)
+    iqa.iqa_merge(ctx, ds, T, m, PARAMS, ml, ma, msum, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    got = (ml.cpu().numpy(), ma.cpu().numpy(), msum.cpu().numpy())
+    direct = parity.oracle_maps(orc, x, y, NT * m, PARAMS)
+    parity.assert_parity(got, direct, PARAMS)
+    ol, oa, osums = parity.oracle_maps(orc, x, y, NT, PARAMS)
+    el, ea = oracle.merge_tiles(ol, oa, osums, m, PARAMS["C2"], PARAMS["C"])
+    r = direct[2][:, 1] / (direct[2][:, 2] + direct[2][:, 3] + PARAMS["C"])
+    parity.assert_lisi_close(got[0], el.ravel())
+    parity.assert_aug_close(got[1], ea.ravel(), r)
+
+
+def test_merge_rejects_bad_factor(ctx):
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    s = torch.zeros((64, 4), device="cuda", dtype=torch.float64)
+    o = torch.zeros(64, device="cuda")
+    for T, m in ((8, 3), (8, 0), (8, 16)):
+        with pytest.raises(iqa.IqaError) as ei:
+            iqa.iqa_merge(ctx, s, T, m, PARAMS, o, None)
+        assert ei.value.status == iqa.IQA_ERR_INVALID_ARG
+
+
+def test_host_many_pipelined_matches_device_path(ctx, orc):
+    """iqa_both_host_many over mixed pairs (two device slots, uploads overlapped
+    with reductions) gives the device path's bits for every pair."""
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    specs = [(512, 64), (1024, 32), (256, 16), (512, 128), (1024, 64)]
+    pairs, outs, hosts = [], [], []
+    for i, (N, NT) in enumerate(specs):
+        x, y = synth.mixed_batch_pair(i, N, seed=7)
+        hx = torch.from_numpy(x).pin_memory()
+        hy = torch.from_numpy(y).pin_memory()
+        T = N // NT
+        o = (np.full(T * T, np.nan, np.float32), np.full(T * T, np.nan, np.float32),
+             np.full((T * T, 4), np.nan))
+        hosts.append((x, y, hx, hy))
+        outs.append(o)
+        pairs.append(iqa.make_host_pair(hx, hy, N, NT, *o))
+    iqa.iqa_both_host_many(ctx, pairs, iqa.IQA_F32, PARAMS)
+    for (N, NT), (x, y, _, _), o in zip(specs, hosts, outs):
+        dev = parity.gpu_maps(ctx, x, y, NT, PARAMS)
+        assert np.array_equal(o[0], dev[0].ravel()) and np.array_equal(o[1], dev[1].ravel())
+        assert np.array_equal(o[2], dev[2])
+        parity.assert_parity(dev, parity.oracle_maps(orc, x, y, NT, PARAMS), PARAMS)
