@@ -43,6 +43,21 @@ N_IMG = 2048
 N_TILE = 64
 PARAMS = {"C1": 1e-6, "C2": 1e-6, "C": 1e-6, "D": 0.5e-6}
 PAPER_NT_SWEEP = (16, 32, 64, 128, 256)
+
+# DRAM traffic of the timed kernel from one ncu capture (summary and command in
+# profiles/iqa_stream_kernel_N2048_NT64_batch8_f32.md): dram__bytes_read.sum +
+# dram__bytes_write.sum of a launch over 8 pairs, per pair.  Valid only for the
+# kernel sources it was taken on: `traffic` is reported as null when their
+# hash no longer matches.
+PROFILED_TRAFFIC = {
+    "sources": ["paper_2501_10653_gb300/csrc/iqa_device.cuh",
+                "paper_2501_10653_gb300/csrc/iqa_stream.cuh",
+                "paper_2501_10653_gb300/csrc/iqa_stream_launch.cuh",
+                "paper_2501_10653_gb300/csrc/iqa_stream_f32.cu"],
+    "sha256": "52dc439a77057917c4d15f88d9b18838d145cfa842110c3c0a7fe79fdbb9da87",
+    "bytes_per_pair": (268486912 + 3892736) / 8,
+    "capture": "8 pairs per launch, scaled by pairs to the timed launch",
+}
 PAPER_H100 = {"lisi_kernel_ms": 0.101, "auglisi_kernel_ms": 0.091,
               "hardware": "H100", "note": "context only (another machine)"}
 
@@ -109,6 +124,20 @@ def sum_over_ranks(v, world, device=None):
 
 # --------------------------------------------------------------------------
 # measured peaks and clocks
+
+def profiled_traffic(pairs_per_launch):
+    import hashlib
+    h = hashlib.sha256()
+    try:
+        for f in PROFILED_TRAFFIC["sources"]:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    if h.hexdigest() != PROFILED_TRAFFIC["sha256"]:
+        return None
+    return int(round(PROFILED_TRAFFIC["bytes_per_pair"] * pairs_per_launch))
+
 
 def measured_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -417,7 +446,10 @@ def run_ours(args):
             "gpu_launches": K,
             "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
-                         "traffic": None, "peak_source": peak_src,
+                         "traffic": profiled_traffic(B),
+                         "algorithmic_bytes": B * pair_bytes,
+                         "traffic_source": "ncu, %s" % PROFILED_TRAFFIC["capture"],
+                         "peak_source": peak_src,
                          "kernel": "iqa_stream_kernel<float,%d,1,1> (persistent, TMA)"
                                    % info["config"]["threads"]},
             "cpu_baseline": cpu,

@@ -141,14 +141,18 @@ static iqa_status plan_capture(iqa_plan *pl)
     return IQA_OK;
 }
 
+// Batched-kernel shape when nothing was tuned: the autotuner's usual choice on
+// GB300 (three CTAs per SM, each a 128-thread consumer group with a two-stage
+// ring of 16 KB per image).
 TileConfig default_batch_config()
 {
     TileConfig c;
     c.variant = 1;
-    c.threads = 256;
-    c.stages = 3;
+    c.threads = 128;
+    c.stages = 2;
     c.stage_kb = 16;
-    c.ctas_per_sm = 2;
+    c.ctas_per_sm = 3;
+    c.unit_kpx = 16;
     return c;
 }
 
