@@ -68,12 +68,16 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--batch", type=int, default=16,
+    ap.add_argument("--batch", type=int, default=32,
                     help="distinct N=2048 pairs per step (one persistent launch)")
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="bound on the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the N=8192 FP32/FP16/BF16 precision and throughput report")
+    ap.add_argument("--precision-batch", type=int, default=16,
+                    help="N=8192 pairs per launch in the precision throughput report")
     ap.add_argument("--tune-iters", type=int, default=3,
                     help="launches per autotuner candidate (0: keep the default shape)")
     return ap.parse_args(argv)
@@ -269,6 +273,75 @@ def _time_plan(iqa, ctx, plan, stream, K, warmup):
     return e0.elapsed_time(e1)
 
 
+def precision_report(iqa, ctx, params, stream, batch=16):
+    """The precision workload (N=8192, N_T=64, point + extended sources, 1e4
+    dynamic range, sigma 5e-3): per-tile error of the FP32 / FP16 / BF16 storage
+    maps against the FP64 oracle on the FP32 originals (storage + accumulation)
+    and on the rounded inputs (accumulation only), and the batched throughput
+    of each storage type."""
+    import torch
+    import oracle
+    from paper_2501_10653_gb300 import synth
+    N, NT = 8192, 64
+    T = N // NT
+    orc = oracle.Oracle()
+    thr = (os.cpu_count() or 1) if orc.has_openmp else 1
+    x32, y32 = synth.precision_pair(0)
+    ol, oa, osum = orc.maps(x32, y32, NT, PARAMS["C1"], PARAMS["C2"], PARAMS["C"],
+                            PARAMS["D"], threads=thr)
+    r32 = osum[:, 1] / (osum[:, 2] + osum[:, 3] + PARAMS["C"])
+    out = {"workload": "N=8192 N_T=64, 33 sources (half extended, sigma 5-40 px), peak "
+                       "flux 1e-4..1, noise sigma 5e-3, 10% of sources dropped"}
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def widen(a):
+        return (a.astype(np.uint32) << 16).view(np.float32) if a.dtype == np.uint16 \
+            else a.astype(np.float32)
+
+    for name, code, dt in (("f32", iqa.IQA_F32, "f32"), ("f16", iqa.IQA_F16, "f16"),
+                           ("bf16", iqa.IQA_BF16, "bf16")):
+        x, y = synth._cast(x32.astype(np.float64), dt), synth._cast(y32.astype(np.float64), dt)
+        tx = torch.from_numpy(x.view(np.int16) if x.dtype == np.uint16 else x).to(dev)
+        ty = torch.from_numpy(y.view(np.int16) if y.dtype == np.uint16 else y).to(dev)
+        lm = torch.empty(T * T, device=dev)
+        am = torch.empty(T * T, device=dev)
+        iqa.iqa_both(ctx, tx, ty, code, N, NT, params, lm, am, None, stream)
+        torch.cuda.synchronize()
+        gl = lm.cpu().numpy().astype(np.float64)
+        ga = am.cpu().numpy().astype(np.float64)
+        rl, ra, rsum = orc.maps(widen(x), widen(y), NT, PARAMS["C1"], PARAMS["C2"],
+                                PARAMS["C"], PARAMS["D"], threads=thr)
+        rr = rsum[:, 1] / (rsum[:, 2] + rsum[:, 3] + PARAMS["C"])
+        nz = ol.ravel() > 0
+        st_l = np.abs(gl - ol.ravel())[nz] / ol.ravel()[nz]
+        st_a = np.abs(ga - oa.ravel()) / np.maximum(np.abs(oa.ravel()), r32)
+        ac_l = np.abs(gl - rl.ravel())[rl.ravel() > 0] / rl.ravel()[rl.ravel() > 0]
+        ac_a = np.abs(ga - ra.ravel()) / np.maximum(np.abs(ra.ravel()), rr)
+        # batched throughput: `batch` distinct device pairs of this storage type
+        B = batch
+        xs = [tx] + [tx.clone() for _ in range(B - 1)]
+        ys = [ty] + [ty.clone() for _ in range(B - 1)]
+        outs = [(torch.empty(T * T, device=dev), torch.empty(T * T, device=dev))
+                for _ in range(B)]
+        pairs = [iqa.make_pair(xs[i], ys[i], N, NT, *outs[i]) for i in range(B)]
+        plan = iqa.iqa_plan_create(ctx, pairs, code, params, iqa.IQA_PLAN_GRAPH)
+        ms = _time_plan(iqa, ctx, plan, stream, 20, 3)
+        iqa.iqa_plan_destroy(plan)
+        es = 4 if name == "f32" else 2
+        out[name] = {
+            "storage_error_vs_fp32_originals": {
+                "lisi_rel_max": float(st_l.max()), "lisi_rel_median": float(np.median(st_l)),
+                "aug_max": float(st_a.max()), "aug_median": float(np.median(st_a))},
+            "accumulation_error_vs_rounded_inputs": {
+                "lisi_rel_max": float(ac_l.max()), "aug_max": float(ac_a.max())},
+            "batched_GBs": round(20 * B * 2 * N * N * es / (ms * 1e-3) / 1e9, 1),
+            "pixel_pairs_per_s": round(20 * B * N * N / (ms * 1e-3), 1),
+        }
+        del xs, ys, outs, tx, ty
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -369,6 +442,10 @@ def run_ours(args):
         sweep[str(nt)] = round(max(10, min(K, 200)) * B * pair_bytes / (ms * 1e-3) / 1e9, 1)
         iqa.iqa_plan_destroy(pl)
 
+    prec = None
+    if rank == 0 and world == 1 and not args.no_precision:
+        prec = precision_report(iqa, ctx, params, stream, args.precision_batch)
+
     # end to end through the host-buffer entry point: one call per step over
     # the same B pairs in page-locked host memory, uploads pipelined with the
     # reductions, maps read back
@@ -453,6 +530,7 @@ def run_ours(args):
                          "kernel": "iqa_stream_kernel<float,%d,1,1> (persistent, TMA)"
                                    % info["config"]["threads"]},
             "cpu_baseline": cpu,
+            "precision_N8192": prec,
             "paper_context": PAPER_H100,
         }
     iqa.iqa_plan_destroy(plan)

@@ -157,43 +157,92 @@ __device__ __forceinline__ float rcp_approx(float v)
     return r;
 }
 
-// Per-pixel terms of Eq. 1 / Eq. 2 for VEC pixel pairs, summed pairwise.
-// Clamp: fmaxf(v, 0) returns 0 for v <= 0 and for NaN (the non-NaN operand).
-// With both pixels clamped, |x + y| = x + y.  The divide s / (d + C1) is
-// s * rcp(d + C1): the denominator is >= C1 > 0, and the product carries at
-// most about 2 ulp (the reciprocal's error plus one rounding).
-template <int VEC, bool DO_A, bool DO_B>
-__device__ __forceinline__ void pixel_terms(const float (&xv)[VEC],
-                                            const float (&yv)[VEC], float C1f,
-                                            float &a, float &b, float &sx,
-                                            float &sy)
+// Per-pixel terms of Eq. 1 / Eq. 2 for the VEC pixel pairs of one 16-byte
+// vector of each image, summed in element order into (a, b, sx, sy):
+//   a = sum s / (d + C1),  b = sum s * d,  sx = sum x,  sy = sum y
+// with x, y clamped, s = x + y (= |x + y| after the clamp) and d = |x - y|.
+// Clamp: max(v, 0) returns 0 for v <= 0 and for NaN (the non-NaN operand);
+// 16-bit pixels are clamped two at a time in their packed form, then widened
+// to float exactly.  The divide s / (d + C1) is s * rcp(d + C1) (denominator
+// >= C1 > 0; about 2 ulp), fused into the accumulation, as is s * d.  The
+// even and odd elements of a vector are summed separately, two at a time with
+// the packed f32x2 operations (add.f32x2, fma.f32x2), then added.
+template <typename T, int VEC, bool DO_A, bool DO_B>
+__device__ __forceinline__ void vector_terms(const Raw<T, VEC> &rx, const Raw<T, VEC> &ry,
+                                             float C1f, float &a, float &b, float &sx,
+                                             float &sy)
 {
-    float ta[VEC], tb[VEC], tx[VEC], ty[VEC];
+    float xv[VEC], yv[VEC];
+    if constexpr (VEC > 1 && !std::is_same<T, float>::value) {
+        // packed clamp of two 16-bit pixels per instruction
+        const uint32_t wx[4] = {rx.v.x, rx.v.y, rx.v.z, rx.v.w};
+        const uint32_t wy[4] = {ry.v.x, ry.v.y, ry.v.z, ry.v.w};
 #pragma unroll
-    for (int i = 0; i < VEC; ++i) {
-        float xc = fmaxf(xv[i], 0.0f);
-        float yc = fmaxf(yv[i], 0.0f);
-        float s = xc + yc;
-        float d = fabsf(xc - yc);
-        ta[i] = DO_A ? s * rcp_approx(d + C1f) : 0.0f;
-        tb[i] = DO_B ? s * d : 0.0f;
-        tx[i] = xc;
-        ty[i] = yc;
-    }
+        for (int w = 0; w < 4; ++w) {
+            if constexpr (std::is_same<T, __half>::value) {
+                const __half2 z = __float2half2_rn(0.0f);
+                __half2 hx = __hmax2(*reinterpret_cast<const __half2 *>(&wx[w]), z);
+                __half2 hy = __hmax2(*reinterpret_cast<const __half2 *>(&wy[w]), z);
+                float2 fx = __half22float2(hx), fy = __half22float2(hy);
+                xv[2 * w] = fx.x;
+                xv[2 * w + 1] = fx.y;
+                yv[2 * w] = fy.x;
+                yv[2 * w + 1] = fy.y;
+            } else {
+                const __nv_bfloat162 z = __float2bfloat162_rn(0.0f);
+                __nv_bfloat162 hx =
+                    __hmax2(*reinterpret_cast<const __nv_bfloat162 *>(&wx[w]), z);
+                __nv_bfloat162 hy =
+                    __hmax2(*reinterpret_cast<const __nv_bfloat162 *>(&wy[w]), z);
+                uint32_t ux = *reinterpret_cast<uint32_t *>(&hx);
+                uint32_t uy = *reinterpret_cast<uint32_t *>(&hy);
+                b2_to_f(ux, xv[2 * w], xv[2 * w + 1]);
+                b2_to_f(uy, yv[2 * w], yv[2 * w + 1]);
+            }
+        }
+    } else {
+        unpack<T, VEC>(rx, xv);
+        unpack<T, VEC>(ry, yv);
 #pragma unroll
-    for (int w = VEC / 2; w >= 1; w >>= 1) {
-#pragma unroll
-        for (int i = 0; i < w; ++i) {
-            if (DO_A) ta[i] += ta[i + w];
-            if (DO_B) tb[i] += tb[i + w];
-            tx[i] += tx[i + w];
-            ty[i] += ty[i + w];
+        for (int i = 0; i < VEC; ++i) {
+            xv[i] = fmaxf(xv[i], 0.0f);
+            yv[i] = fmaxf(yv[i], 0.0f);
         }
     }
-    a = ta[0];
-    b = tb[0];
-    sx = tx[0];
-    sy = ty[0];
+    if constexpr (VEC == 1) {
+        const float s = xv[0] + yv[0];
+        const float d = fabsf(xv[0] - yv[0]);
+        a = DO_A ? s * rcp_approx(d + C1f) : 0.0f;
+        b = DO_B ? s * d : 0.0f;
+        sx = xv[0];
+        sy = yv[0];
+    } else {
+        // two pixel pairs per instruction with the packed FP32 operations of
+        // this architecture; even and odd elements form two partial sums
+        const float2 neg1 = make_float2(-1.0f, -1.0f);
+        const float2 c1 = make_float2(C1f, C1f);
+        float2 a2 = make_float2(0.0f, 0.0f), b2 = a2, x2s = a2, y2s = a2;
+#pragma unroll
+        for (int i = 0; i < VEC; i += 2) {
+            const float2 x2 = make_float2(xv[i], xv[i + 1]);
+            const float2 y2 = make_float2(yv[i], yv[i + 1]);
+            const float2 s2 = __fadd2_rn(x2, y2);
+            const float2 m2 = __ffma2_rn(y2, neg1, x2);  // x - y, one rounding
+            const float2 d2 = make_float2(fabsf(m2.x), fabsf(m2.y));
+            if (DO_A) {
+                const float2 t2 = __fadd2_rn(d2, c1);
+                const float2 r2 = make_float2(rcp_approx(t2.x), rcp_approx(t2.y));
+                a2 = __ffma2_rn(s2, r2, a2);
+            }
+            if (DO_B) b2 = __ffma2_rn(s2, d2, b2);
+            x2s = __fadd2_rn(x2s, x2);
+            y2s = __fadd2_rn(y2s, y2);
+        }
+        a = a2.x + a2.y;
+        b = b2.x + b2.y;
+        sx = x2s.x + x2s.y;
+        sy = y2s.x + y2s.y;
+    }
 }
 
 // Kahan-compensated float accumulator.
@@ -248,12 +297,9 @@ __device__ __forceinline__ void accumulate_unit(const T *__restrict__ xu,
         float ba = 0.0f, bb = 0.0f, bx = 0.0f, by = 0.0f;
 #pragma unroll
         for (int u = 0; u < ILP; ++u) {
-            float xv[VEC], yv[VEC];
-            unpack<T, VEC>(rx[u], xv);
-            unpack<T, VEC>(ry[u], yv);
             float a, b, sx, sy;
             // a vector that was not loaded is all zeros and adds exactly 0
-            pixel_terms<VEC, DO_A, DO_B>(xv, yv, C1f, a, b, sx, sy);
+            vector_terms<T, VEC, DO_A, DO_B>(rx[u], ry[u], C1f, a, b, sx, sy);
             ba += a;
             bb += b;
             bx += sx;

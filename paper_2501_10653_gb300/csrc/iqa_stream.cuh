@@ -333,11 +333,8 @@ __global__ void __launch_bounds__(CT + 32, 1)
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                float xv[VEC], yv[VEC];
-                unpack<T, VEC>(rx[j], xv);
-                unpack<T, VEC>(ry[j], yv);
                 float a, b, sx, sy;
-                pixel_terms<VEC, DO_A, DO_B>(xv, yv, C1f, a, b, sx, sy);
+                vector_terms<T, VEC, DO_A, DO_B>(rx[j], ry[j], C1f, a, b, sx, sy);
                 ba += a;
                 bb += b;
                 bx += sx;

@@ -10,10 +10,11 @@ per-tile quantity within 1e-5 relative.
 * sums A, B, Sx, Sy: each within 1e-5 relative; all terms are nonnegative, so
   the sums are perfectly conditioned; an oracle 0 must come back exactly 0.
 The bound follows from the arithmetic: each per-pixel term carries a few
-float32 roundings (<= ~4 u plus <= 2 ulp for the fast divide, u = 2^-24), the
-per-thread sums are pairwise within a vector, sequential over at most 8
-vectors and Kahan-folded (<= ~12 u), and the cross-thread tree is <= 16 float32
-additions then FP64, so the worst case is about 40 u = 2.4e-6, inside 1e-5.
+float32 roundings (<= ~4 u plus ~2 ulp for the approximate reciprocal,
+u = 2^-24); a thread sums a vector's <= 8 terms in order (<= 7 u), then <= 8
+vector partials in order (<= 7 u), Kahan-folded across batches (~2 u); the
+cross-thread shuffle trees and the cluster combine add <= ~16 float32
+additions.  The worst case is about 40 u = 2.4e-6, inside 1e-5.
 """
 import numpy as np
 

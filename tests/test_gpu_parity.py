@@ -380,3 +380,38 @@ def test_host_many_pipelined_matches_device_path(ctx, orc):
         assert np.array_equal(o[0], dev[0].ravel()) and np.array_equal(o[1], dev[1].ravel())
         assert np.array_equal(o[2], dev[2])
         parity.assert_parity(dev, parity.oracle_maps(orc, x, y, NT, PARAMS), PARAMS)
+
+
+@pytest.mark.parametrize("dt", ["f16", "bf16"])
+def test_full_size_16bit_sampled_tiles(ctx, orc, dt):
+    """N = 8192, N_T = 64 with 16-bit storage (the precision workload's size):
+    sampled tiles against the oracle on the rounded inputs (the accumulation
+    bound, 1e-5 relative)."""
+    x, y = synth.precision_pair(0, dtype=dt)
+    N, NT = 8192, 64
+    T = N // NT
+    got = parity.gpu_maps(ctx, x, y, NT, PARAMS)
+    rng = np.random.default_rng(10)
+    pick = np.unique(np.concatenate([rng.integers(0, T * T, 150), [0, T * T - 1]]))
+    osums = orc.tile_sums(parity.widen(x), parity.widen(y), NT, PARAMS["C1"], tiles=pick)
+    A, B, Sx, Sy = osums.T
+    D = PARAMS["C1"] / 2
+    r = B / (Sx + Sy + PARAMS["C"])
+    parity.assert_lisi_close(got[0].ravel()[pick], D * A / (np.maximum(Sx, Sy) + PARAMS["C2"]))
+    parity.assert_aug_close(got[1].ravel()[pick], 1 - r, r)
+    parity.assert_sums_close(got[2][pick], osums)
+
+
+@pytest.mark.parametrize("dt", ["f16", "bf16"])
+def test_16bit_nan_and_negative_pixels_read_as_zero(ctx, orc, dt):
+    """16-bit pixels are clamped in packed form: NaN and negatives read as 0."""
+    x, y = synth.paper_pair(N=512, dtype=dt)
+    x = x.copy()
+    y = y.copy()
+    rng = np.random.default_rng(6)
+    nan_bits = np.uint16(0x7E00) if dt == "f16" else np.uint16(0x7FC0)
+    for a in (x, y):
+        v = a.view(np.uint16)
+        v[rng.random(v.shape) < 0.02] = nan_bits
+    want = parity.oracle_maps(orc, x, y, 64, PARAMS)
+    parity.assert_parity(parity.gpu_maps(ctx, x, y, 64, PARAMS), want, PARAMS)
