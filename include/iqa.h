@@ -365,6 +365,116 @@ iqa_status iqa_wait(iqa_ctx *ctx, iqa_stream stream, int timeout_us);
 iqa_status iqa_batch_noalloc(const iqa_pair *pairs, int npairs, iqa_dtype dtype,
                              const iqa_params *params, iqa_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * Serving loop: continuous batching of image-pair requests.
+ *
+ * Reference skies (first epochs) stay resident on the device.  A request names
+ * a reference, a tile side and a seed; its second epoch is rendered on the
+ * device from the reference's catalogue (minus the sources the request drops,
+ * plus an optional transient) over fresh seeded noise, then the pair's LISI
+ * and augLISI maps are computed (Eq. 1, Eq. 2).  A native worker thread
+ * admits pending requests in arrival order while they fit the device pool
+ * (the admission budget) and the step has room, and launches each step as one
+ * CUDA graph: the work-list uploads, one generator launch and one persistent
+ * map kernel over all the step's pairs.  Up to max_inflight_steps steps run
+ * at once on separate streams, so requests that arrive while others are on
+ * the GPU join the next step as memory and slots free up.  A request's maps
+ * do not depend on which other requests shared its step.
+ */
+typedef struct iqa_server iqa_server;
+typedef unsigned long long iqa_handle;
+
+/* A reference catalogue: Gaussian-beam sources at integer centres, each with a
+ * float32 1-D profile g[-h..h]; source i adds (flux_i * g[dy]) * g[dx] to the
+ * pixel at offset (dy, dx) from its centre.  All arrays are host memory and
+ * are copied. */
+typedef struct {
+    int N;                  /* image side, a multiple of 16 */
+    int nsrc;
+    const int *x;           /* source centres, columns */
+    const int *y;           /* source centres, rows */
+    const float *flux;      /* peak flux */
+    const int *half;        /* profile half-width h (window 2h+1, h <= 64) */
+    const int *profile_off; /* start of source i's profile in `profile` */
+    const float *profile;
+    int nprofile;           /* floats in `profile` */
+    float noise_sigma;      /* sigma of each epoch's noise */
+} iqa_catalog;
+
+typedef struct {
+    iqa_dtype dtype;           /* storage of references and epochs */
+    int max_pairs_per_step;    /* 1..64 */
+    int max_inflight_steps;    /* 1..4 */
+    size_t pool_bytes;         /* device memory for second epochs: the admission
+                                  budget (a request needs N*N elements) */
+    int one_pair_per_launch;   /* 1: the plain path as a baseline -- one request
+                                  per step, the streaming-load kernel, no graph */
+    int simulate;              /* 1: no GPU work; a step completes after
+                                  bytes / sim_bytes_per_s (host-side tests);
+                                  2: steps never complete (a stalled source) */
+    double sim_bytes_per_s;
+    double step_timeout_ms;    /* host watchdog: a step still running after this
+                                  fails its requests with IQA_ERR_TIMEOUT (its
+                                  buffers stay reserved until it ends); 0 = 10 s */
+    iqa_params params;
+} iqa_server_config;
+
+typedef struct {
+    int ref_id;                /* a reference added with iqa_server_add_reference */
+    int NT;                    /* tile side: divides N, multiple of 16 bytes, <= 256 */
+    unsigned long long seed;   /* noise seed of the second epoch */
+    int ndrop;                 /* 0..8 catalogue sources left out of epoch 2 */
+    int drop[8];
+    int add_src;               /* -1, or a source whose profile a transient uses */
+    int add_x, add_y;          /* transient centre */
+    float add_flux;            /* transient peak flux */
+} iqa_request;
+
+typedef struct {
+    long long submitted, completed, failed, pending, inflight, steps;
+    double p50_ms, p99_ms, max_ms, mean_ms;  /* submit -> maps on the host */
+    double pairs_per_s;        /* completed / (last completion - first submit) */
+    double input_gb_per_s;     /* algorithmic input bytes of completed pairs / s */
+    double mean_pairs_per_step;
+    unsigned long long pool_bytes, pool_peak_bytes;
+} iqa_server_stats;
+
+/* Creates a server on ctx's device (ctx may be NULL with simulate = 1) and
+ * starts its worker thread.  Allocates the pool and per-step buffers.
+ * Errors: IQA_ERR_INVALID_ARG, IQA_ERR_NOMEM, IQA_ERR_CUDA. */
+iqa_status iqa_server_create(iqa_ctx *ctx, const iqa_server_config *cfg,
+                             iqa_server **out);
+
+/* Renders the reference's first epoch on the device (seed `seed`) and keeps it
+ * and its catalogue resident under `ref_id`.  Synchronous.
+ * Errors: IQA_ERR_INVALID_ARG (bad catalogue or id in use), IQA_ERR_NOMEM. */
+iqa_status iqa_server_add_reference(iqa_server *srv, int ref_id, const iqa_catalog *cat,
+                                    unsigned long long seed);
+
+/* Copies a resident reference image (N*N storage elements) to host memory. */
+iqa_status iqa_server_reference_image(iqa_server *srv, int ref_id, void *host_out);
+
+/* Queues a request; *out identifies it.  Returns at once.
+ * Errors: IQA_ERR_INVALID_ARG (unknown reference, bad N_T or drop list),
+ * IQA_ERR_NOMEM (the request alone exceeds the pool), IQA_ERR_BUSY (queue full). */
+iqa_status iqa_submit(iqa_server *srv, const iqa_request *req, iqa_handle *out);
+
+/* Waits at most timeout_us (0: just look) for the request.  Returns IQA_OK
+ * (maps ready), IQA_PENDING (not yet), IQA_ERR_TIMEOUT (a device-side wait of
+ * its step ran out, see IQA_OPT_WAIT_TIMEOUT_US), IQA_ERR_CUDA, or
+ * IQA_ERR_INVALID_ARG (unknown handle). */
+iqa_status iqa_poll(iqa_server *srv, iqa_handle h, int timeout_us);
+
+/* For a finished request: copies its maps ((N/NT)^2 float32 each, either
+ * pointer may be NULL) and its latency, then forgets the request. */
+iqa_status iqa_result(iqa_server *srv, iqa_handle h, float *lisi_map, float *aug_map,
+                      double *latency_ms);
+
+iqa_status iqa_server_get_stats(iqa_server *srv, iqa_server_stats *out);
+
+/* Stops the worker after the steps in flight, frees everything. */
+void iqa_server_destroy(iqa_server *srv);
+
 /* Context options for iqa_set_option. */
 typedef enum {
     /* Bound, in microseconds, on every device-side wait of the persistent

@@ -1,0 +1,931 @@
+// iqa_server.cpp -- the serving loop: resident reference skies, device-side
+// second epochs, admission by a device-memory budget, continuous batching of
+// requests into steps, one CUDA graph per step slot, p50/p99 latency.
+//
+// A native worker thread owns every GPU action.  Each pass it (1) retires
+// steps whose completion event has fired (maps copied to the requests, pool
+// memory returned), (2) marks steps that ran past the host-side step timeout
+// as failed, and (3) if a step slot is free, admits pending requests in
+// arrival order while they fit the pool and the step, and launches the step:
+// fill the slot's page-locked work tables, replay the slot's graph (table
+// uploads -> epoch generator -> persistent map kernel, all reading their work
+// counts from device memory), read the maps back, record the event.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "iqa.h"
+#include "iqa_ctx.h"
+#include "iqa_stream.cuh"
+#include "iqa_synth.h"
+
+namespace iqa {
+TileConfig default_batch_config();
+}
+
+using namespace iqa;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_between(Clock::time_point a, Clock::time_point b)
+{
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// First-fit allocator over the offsets [0, size) of the device pool.
+class RangeAllocator {
+public:
+    void reset(size_t size)
+    {
+        size_ = size;
+        used_ = peak_ = 0;
+        free_.clear();
+        if (size) free_[0] = size;
+    }
+    bool alloc(size_t bytes, size_t *off)
+    {
+        bytes = round_up(bytes, 256);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < bytes) continue;
+            *off = it->first;
+            const size_t rest = it->second - bytes, start = it->first + bytes;
+            free_.erase(it);
+            if (rest) free_[start] = rest;
+            used_ += bytes;
+            peak_ = std::max(peak_, used_);
+            return true;
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes)
+    {
+        bytes = round_up(bytes, 256);
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t size() const { return size_; }
+    size_t peak() const { return peak_; }
+
+private:
+    size_t size_ = 0, used_ = 0, peak_ = 0;
+    std::map<size_t, size_t> free_;
+};
+
+struct Reference {
+    int N = 0;
+    int nsrc = 0;
+    SynthCatalog *d_cat = nullptr;  // device struct
+    void *d_arrays = nullptr;       // catalogue arrays
+    void *d_image = nullptr;        // resident first epoch
+};
+
+enum ReqState { REQ_PENDING, REQ_INFLIGHT, REQ_DONE, REQ_FAILED };
+
+struct Request {
+    iqa_handle h = 0;
+    iqa_request r{};
+    int N = 0, T = 0;
+    size_t epoch_bytes = 0, pool_off = 0;
+    ReqState state = REQ_PENDING;
+    iqa_status status = IQA_PENDING;
+    Clock::time_point t_submit, t_done;
+    std::vector<float> lisi, aug;
+};
+
+struct Slot {
+    bool busy = false;
+    bool timed_out = false;
+    std::vector<std::shared_ptr<Request>> reqs;
+    size_t out_floats = 0;
+    unsigned long long bytes = 0;
+    Clock::time_point t_launch;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    SynthJob *d_jobs = nullptr, *h_jobs = nullptr;
+    long long *d_synth_hdr = nullptr, *h_synth_hdr = nullptr;
+    PairDesc *d_pairs = nullptr, *h_pairs = nullptr;
+    long long *d_dyn = nullptr, *h_dyn = nullptr;
+    unsigned long long *d_sched = nullptr;
+    int *d_status = nullptr, *h_status = nullptr;
+    float *d_out = nullptr, *h_out = nullptr;
+    size_t out_cap = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
+struct iqa_server {
+    iqa_ctx *ctx = nullptr;
+    iqa_server_config cfg{};
+    iqa_params P{};
+    TileConfig kcfg;  // persistent-kernel shape
+    int es = 4;
+    int synth_grid = 0;
+    int device = 0;
+    double step_timeout_ms = 10000.0;
+
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    std::thread worker;
+
+    std::unordered_map<int, Reference> refs;
+    std::deque<std::shared_ptr<Request>> pending;
+    std::unordered_map<iqa_handle, std::shared_ptr<Request>> all;
+    iqa_handle next_handle = 1;
+    std::vector<Slot> slots;
+    RangeAllocator pool;
+    void *d_pool = nullptr;
+
+    // statistics
+    long long submitted = 0, completed = 0, failed = 0, steps = 0, step_pairs = 0;
+    std::vector<double> latencies;
+    double bytes_done = 0.0;
+    bool have_first = false;
+    Clock::time_point t_first, t_last;
+    std::string worker_error;
+};
+
+namespace {
+
+const size_t kMaxQueue = 1 << 20;
+
+void free_slot(Slot &s)
+{
+    if (s.exec) cudaGraphExecDestroy(s.exec);
+    if (s.graph) cudaGraphDestroy(s.graph);
+    cudaFree(s.d_jobs);
+    cudaFree(s.d_synth_hdr);
+    cudaFree(s.d_pairs);
+    cudaFree(s.d_dyn);
+    cudaFree(s.d_sched);
+    cudaFree(s.d_status);
+    cudaFree(s.d_out);
+    cudaFreeHost(s.h_jobs);
+    cudaFreeHost(s.h_synth_hdr);
+    cudaFreeHost(s.h_pairs);
+    cudaFreeHost(s.h_dyn);
+    cudaFreeHost(s.h_status);
+    cudaFreeHost(s.h_out);
+    if (s.ev) cudaEventDestroy(s.ev);
+    if (s.st) cudaStreamDestroy(s.st);
+    s = Slot();
+}
+
+StreamParams slot_stream_params(const iqa_server *srv, const Slot &s)
+{
+    StreamParams sp;
+    std::memset(&sp, 0, sizeof sp);
+    sp.descs = s.d_pairs;
+    sp.stage_bytes = srv->kcfg.stage_kb * 1024;
+    sp.stages = srv->kcfg.stages;
+    sp.status = s.d_status;
+    sp.timeout_ns = srv->ctx->wait_timeout_ns;
+    sp.sched = s.d_sched;
+    sp.inject_stall = srv->ctx->inject_stall;
+    sp.dyn = s.d_dyn;
+    return sp;
+}
+
+// The slot's graph: work-table uploads, the epoch generator and the
+// persistent map kernel, all sized from device-side headers.
+cudaError_t capture_slot(iqa_server *srv, Slot &s)
+{
+    const int M = srv->cfg.max_pairs_per_step;
+    cudaError_t e = cudaStreamBeginCapture(s.st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t e1 = cudaMemcpyAsync(s.d_jobs, s.h_jobs, sizeof(SynthJob) * M,
+                                     cudaMemcpyHostToDevice, s.st);
+    if (e1 == cudaSuccess)
+        e1 = cudaMemcpyAsync(s.d_synth_hdr, s.h_synth_hdr, 16, cudaMemcpyHostToDevice, s.st);
+    if (e1 == cudaSuccess)
+        e1 = cudaMemcpyAsync(s.d_pairs, s.h_pairs, sizeof(PairDesc) * M,
+                             cudaMemcpyHostToDevice, s.st);
+    if (e1 == cudaSuccess)
+        e1 = cudaMemcpyAsync(s.d_dyn, s.h_dyn, 16, cudaMemcpyHostToDevice, s.st);
+    if (e1 == cudaSuccess)
+        e1 = launch_synth((int)srv->cfg.dtype, s.d_jobs, s.d_synth_hdr, srv->synth_grid, s.st);
+    if (e1 == cudaSuccess) {
+        StreamParams sp = slot_stream_params(srv, s);
+        const int grid = srv->ctx->num_sms * srv->kcfg.ctas_per_sm;
+        e1 = launch_stream(sp, srv->cfg.dtype, srv->kcfg, MAPS_AB, grid, s.st);
+    }
+    e = cudaStreamEndCapture(s.st, &s.graph);
+    if (e1 != cudaSuccess) return e1;
+    if (e != cudaSuccess) return e;
+    return cudaGraphInstantiate(&s.exec, s.graph, 0);
+}
+
+cudaError_t alloc_slot(iqa_server *srv, Slot &s)
+{
+    const int M = srv->cfg.max_pairs_per_step;
+    cudaError_t e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_jobs, sizeof(SynthJob) * M);
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_synth_hdr, 16);
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_pairs, sizeof(PairDesc) * M);
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_dyn, 16);
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_sched, 256);
+    if (e == cudaSuccess) e = cudaMemset(s.d_sched, 0, 256);
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_status, 256);
+    if (e == cudaSuccess) e = cudaMemset(s.d_status, 0, 256);
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_jobs, sizeof(SynthJob) * M);
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_synth_hdr, 16);
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_pairs, sizeof(PairDesc) * M);
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_dyn, 16);
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_status, 256);
+    if (e == cudaSuccess) {
+        std::memset(s.h_jobs, 0, sizeof(SynthJob) * M);
+        std::memset(s.h_pairs, 0, sizeof(PairDesc) * M);
+        std::memset(s.h_synth_hdr, 0, 16);
+        std::memset(s.h_dyn, 0, 16);
+    }
+    if (e == cudaSuccess) e = cudaMemset(s.d_dyn, 0, 16);
+    if (e == cudaSuccess) e = cudaMemset(s.d_synth_hdr, 0, 16);
+    if (e == cudaSuccess && !srv->cfg.one_pair_per_launch) {
+        // one launch of each kernel with empty work before capture, so that
+        // launch attributes are set outside the capture
+        e = launch_synth((int)srv->cfg.dtype, s.d_jobs, s.d_synth_hdr, srv->synth_grid, s.st);
+        if (e == cudaSuccess) {
+            StreamParams sp = slot_stream_params(srv, s);
+            e = launch_stream(sp, srv->cfg.dtype, srv->kcfg, MAPS_AB,
+                              srv->ctx->num_sms * srv->kcfg.ctas_per_sm, s.st);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s.st);
+        if (e == cudaSuccess) e = capture_slot(srv, s);
+    }
+    return e;
+}
+
+// Makes room for the step's maps in the slot's device and page-locked buffers.
+cudaError_t ensure_out(Slot &s, size_t floats)
+{
+    if (floats <= s.out_cap) return cudaSuccess;
+    size_t cap = std::max(floats, s.out_cap * 2);
+    cudaFree(s.d_out);
+    cudaFreeHost(s.h_out);
+    s.d_out = nullptr;
+    s.h_out = nullptr;
+    s.out_cap = 0;
+    cudaError_t e = cudaMalloc(&s.d_out, cap * sizeof(float));
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_out, cap * sizeof(float));
+    if (e == cudaSuccess) s.out_cap = cap;
+    return e;
+}
+
+// Fills the slot's tables for its requests and launches the step.
+iqa_status launch_step(iqa_server *srv, Slot &s)
+{
+    iqa_ctx *ctx = srv->ctx;
+    const bool sim = srv->cfg.simulate != 0;
+    size_t floats = 0;
+    unsigned long long bytes = 0;
+    for (auto &r : s.reqs) {
+        floats += 2 * (size_t)r->T * r->T;
+        bytes += 2ull * r->N * r->N * srv->es;
+    }
+    s.out_floats = floats;
+    s.bytes = bytes;
+    s.t_launch = Clock::now();
+    s.timed_out = false;
+    if (sim) return IQA_OK;
+
+    cudaError_t e = ensure_out(s, floats);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "step output buffers");
+    char *pool = static_cast<char *>(srv->d_pool);
+    long long blocks = 0, units = 0;
+    size_t o = 0;
+    const int n = (int)s.reqs.size();
+    for (int k = 0; k < n; ++k) {
+        Request &r = *s.reqs[k];
+        const Reference &ref = srv->refs.at(r.r.ref_id);
+        void *epoch = pool + r.pool_off;
+        SynthJob &j = s.h_jobs[k];
+        std::memset(&j, 0, sizeof j);
+        j.cat = ref.d_cat;
+        j.out = epoch;
+        j.blocks_begin = blocks;
+        j.seed = r.r.seed;
+        j.N = r.N;
+        j.ndrop = r.r.ndrop;
+        for (int d = 0; d < r.r.ndrop; ++d) j.drop[d] = r.r.drop[d];
+        j.add_src = r.r.add_src;
+        j.add_x = r.r.add_x;
+        j.add_y = r.r.add_y;
+        j.add_flux = r.r.add_flux;
+        blocks += (long long)(r.N / kSynthBlock) * (r.N / kSynthBlock);
+        float *dl = s.d_out + o, *da = s.d_out + o + (size_t)r.T * r.T;
+        o += 2 * (size_t)r.T * r.T;
+        if (srv->cfg.one_pair_per_launch) continue;
+        TileConfig c = srv->kcfg;
+        c.TX = stream_tiles_across(r.N, r.r.NT, srv->cfg.dtype, c.threads,
+                                   (long long)c.unit_kpx * 1024);
+        iqa_status st = fill_pair_desc(ctx, &s.h_pairs[k], ref.d_image, epoch, r.N, r.r.NT,
+                                       srv->cfg.dtype, c, srv->P, dl, da, nullptr, units);
+        if (st != IQA_OK) return st;
+        units += pair_units(r.N, r.r.NT, c);
+    }
+    s.h_synth_hdr[0] = n;
+    s.h_synth_hdr[1] = blocks;
+    s.h_dyn[0] = n;
+    s.h_dyn[1] = units;
+    if (srv->cfg.one_pair_per_launch) {
+        // baseline: the plain path, one pair, no graph
+        Request &r = *s.reqs[0];
+        const Reference &ref = srv->refs.at(r.r.ref_id);
+        e = cudaMemcpyAsync(s.d_jobs, s.h_jobs, sizeof(SynthJob), cudaMemcpyHostToDevice, s.st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s.d_synth_hdr, s.h_synth_hdr, 16, cudaMemcpyHostToDevice, s.st);
+        if (e == cudaSuccess)
+            e = launch_synth((int)srv->cfg.dtype, s.d_jobs, s.d_synth_hdr, srv->synth_grid, s.st);
+        if (e == cudaSuccess) {
+            TileConfig c = pick_config(ctx, r.N, r.r.NT, srv->cfg.dtype, MAPS_AB, true);
+            if (c.variant == 1) {
+                iqa_status st = run_stream_pair(ctx, ref.d_image, pool + r.pool_off,
+                                                srv->cfg.dtype, r.N, r.r.NT, c, srv->P,
+                                                s.d_out, s.d_out + (size_t)r.T * r.T, nullptr,
+                                                MAPS_AB, s.st);
+                if (st != IQA_OK) return st;
+            } else {
+                TileArgs a = make_args(ref.d_image, pool + r.pool_off, r.N, r.r.NT, c, srv->P,
+                                       s.d_out, s.d_out + (size_t)r.T * r.T, nullptr);
+                e = launch_tiles(a, c, srv->cfg.dtype, MAPS_AB, r.T, s.st);
+            }
+        }
+    } else {
+        e = cudaGraphLaunch(s.exec, s.st);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s.h_out, s.d_out, floats * sizeof(float), cudaMemcpyDeviceToHost,
+                            s.st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s.h_status, s.d_status, sizeof(int), cudaMemcpyDeviceToHost, s.st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.d_status, 0, sizeof(int), s.st);
+    if (e == cudaSuccess) e = cudaEventRecord(s.ev, s.st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
+    return IQA_OK;
+}
+
+// True when the slot's step has finished (its GPU work, or its modelled time).
+bool step_finished(iqa_server *srv, Slot &s, iqa_status *st)
+{
+    *st = IQA_OK;
+    if (srv->cfg.simulate) {
+        if (srv->cfg.simulate == 2) return false;  // a completion source that stalls
+        const double need_ms = 1e3 * (double)s.bytes / std::max(1.0, srv->cfg.sim_bytes_per_s);
+        return ms_between(s.t_launch, Clock::now()) >= need_ms;
+    }
+    cudaError_t e = cudaEventQuery(s.ev);
+    if (e == cudaErrorNotReady) return false;
+    if (e != cudaSuccess) {
+        *st = IQA_ERR_CUDA;
+        return true;
+    }
+    if (*s.h_status != 0) *st = IQA_ERR_TIMEOUT;
+    return true;
+}
+
+void finish_request(iqa_server *srv, Request &r, iqa_status st, Clock::time_point now)
+{
+    r.t_done = now;
+    r.status = st;
+    r.state = st == IQA_OK ? REQ_DONE : REQ_FAILED;
+    if (st == IQA_OK) {
+        ++srv->completed;
+        srv->latencies.push_back(ms_between(r.t_submit, now));
+        srv->bytes_done += 2.0 * r.N * r.N * srv->es;
+        srv->t_last = now;
+    } else {
+        ++srv->failed;
+    }
+}
+
+// Called with srv->mu held.
+void retire(iqa_server *srv, Slot &s)
+{
+    iqa_status st;
+    if (!step_finished(srv, s, &st)) {
+        if (!s.timed_out && srv->step_timeout_ms > 0 &&
+            ms_between(s.t_launch, Clock::now()) > srv->step_timeout_ms) {
+            // host-side watchdog: the step's requests fail now; its buffers stay
+            // reserved until its GPU work (if any) really ends
+            s.timed_out = true;
+            const auto now = Clock::now();
+            for (auto &r : s.reqs)
+                if (r->state == REQ_INFLIGHT) finish_request(srv, *r, IQA_ERR_TIMEOUT, now);
+            srv->cv_done.notify_all();
+        }
+        return;
+    }
+    const auto now = Clock::now();
+    size_t o = 0;
+    for (auto &rp : s.reqs) {
+        Request &r = *rp;
+        const size_t n = (size_t)r.T * r.T;
+        if (r.state == REQ_INFLIGHT) {
+            if (st == IQA_OK && !srv->cfg.simulate) {
+                r.lisi.assign(s.h_out + o, s.h_out + o + n);
+                r.aug.assign(s.h_out + o + n, s.h_out + o + 2 * n);
+            } else if (st == IQA_OK) {
+                r.lisi.assign(n, 0.0f);
+                r.aug.assign(n, 0.0f);
+            }
+            finish_request(srv, r, st, now);
+        }
+        o += 2 * n;
+        srv->pool.release(r.pool_off, r.epoch_bytes);
+    }
+    s.reqs.clear();
+    s.busy = false;
+    srv->cv_done.notify_all();
+}
+
+void worker_main(iqa_server *srv)
+{
+    if (!srv->cfg.simulate) cudaSetDevice(srv->device);
+    std::unique_lock<std::mutex> lk(srv->mu);
+    while (true) {
+        bool any_busy = false;
+        for (auto &s : srv->slots) {
+            if (s.busy) retire(srv, s);
+            any_busy = any_busy || s.busy;
+        }
+        if (srv->stop && !any_busy) break;
+        // admit and launch on a free slot
+        Slot *free_slot_p = nullptr;
+        for (auto &s : srv->slots)
+            if (!s.busy) {
+                free_slot_p = &s;
+                break;
+            }
+        bool launched = false;
+        if (!srv->stop && free_slot_p && !srv->pending.empty()) {
+            Slot &s = *free_slot_p;
+            const int cap = srv->cfg.one_pair_per_launch ? 1 : srv->cfg.max_pairs_per_step;
+            while ((int)s.reqs.size() < cap && !srv->pending.empty()) {
+                auto r = srv->pending.front();
+                size_t off = 0;
+                if (!srv->pool.alloc(r->epoch_bytes, &off)) break;  // arrival order kept
+                r->pool_off = off;
+                r->state = REQ_INFLIGHT;
+                srv->pending.pop_front();
+                s.reqs.push_back(r);
+            }
+            if (!s.reqs.empty()) {
+                s.busy = true;
+                iqa_status st = launch_step(srv, s);
+                ++srv->steps;
+                srv->step_pairs += (long long)s.reqs.size();
+                if (st != IQA_OK) {
+                    // nothing was enqueued that will complete: fail and release now
+                    const auto now = Clock::now();
+                    for (auto &r : s.reqs) {
+                        finish_request(srv, *r, st, now);
+                        srv->pool.release(r->pool_off, r->epoch_bytes);
+                    }
+                    srv->worker_error = iqa_last_error(srv->ctx);
+                    s.reqs.clear();
+                    s.busy = false;
+                    srv->cv_done.notify_all();
+                }
+                launched = true;
+            }
+        }
+        if (!launched) {
+            // nothing to launch: wait for new work, polling busy steps often
+            srv->cv_work.wait_for(lk, std::chrono::microseconds(any_busy ? 20 : 2000));
+        }
+    }
+}
+
+iqa_status upload_reference(iqa_server *srv, Reference &ref, const iqa_catalog *cat,
+                            unsigned long long seed)
+{
+    iqa_ctx *ctx = srv->ctx;
+    const int N = cat->N, n = cat->nsrc;
+    const int bpr = (N + kSynthBin - 1) / kSynthBin;
+    // catalogue bins: every source whose window meets a bin, in catalogue order
+    std::vector<std::vector<int>> bins((size_t)bpr * bpr);
+    for (int i = 0; i < n; ++i) {
+        const int h = cat->half[i];
+        const int r0 = std::max(0, cat->y[i] - h) / kSynthBin;
+        const int r1 = std::min(N - 1, cat->y[i] + h) / kSynthBin;
+        const int c0 = std::max(0, cat->x[i] - h) / kSynthBin;
+        const int c1 = std::min(N - 1, cat->x[i] + h) / kSynthBin;
+        for (int br = r0; br <= r1; ++br)
+            for (int bc = c0; bc <= c1; ++bc) bins[(size_t)br * bpr + bc].push_back(i);
+    }
+    std::vector<int> start(bins.size() + 1, 0), flat;
+    for (size_t b = 0; b < bins.size(); ++b) {
+        start[b + 1] = start[b] + (int)bins[b].size();
+        flat.insert(flat.end(), bins[b].begin(), bins[b].end());
+    }
+    if (flat.empty()) flat.push_back(0);
+    // one allocation for every array: x, y, half, poff, flux, profile, bins
+    const size_t sz_i = sizeof(int) * (size_t)std::max(n, 1);
+    size_t off[9];
+    size_t total = 0;
+    const size_t sizes[8] = {sz_i, sz_i, sz_i, sz_i, sizeof(float) * (size_t)std::max(n, 1),
+                             sizeof(float) * (size_t)std::max(cat->nprofile, 1),
+                             sizeof(int) * start.size(), sizeof(int) * flat.size()};
+    for (int k = 0; k < 8; ++k) {
+        off[k] = total;
+        total += round_up(sizes[k], 256);
+    }
+    off[8] = total;
+    total += round_up(sizeof(SynthCatalog), 256);
+    const size_t img_bytes = (size_t)N * N * srv->es;
+    cudaError_t e = cudaMalloc(&ref.d_arrays, total);
+    if (e == cudaSuccess) e = cudaMalloc(&ref.d_image, img_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(ctx, "reference of %zu bytes does not fit: %s", img_bytes + total,
+                  cudaGetErrorString(e));
+        return IQA_ERR_NOMEM;
+    }
+    char *base = static_cast<char *>(ref.d_arrays);
+    const void *src[8] = {cat->x, cat->y, cat->half, cat->profile_off, cat->flux,
+                          cat->profile, start.data(), flat.data()};
+    const size_t copy_sizes[8] = {sizeof(int) * (size_t)n, sizeof(int) * (size_t)n,
+                                  sizeof(int) * (size_t)n, sizeof(int) * (size_t)n,
+                                  sizeof(float) * (size_t)n,
+                                  sizeof(float) * (size_t)cat->nprofile,
+                                  sizeof(int) * start.size(), sizeof(int) * flat.size()};
+    for (int k = 0; k < 8 && e == cudaSuccess; ++k)
+        if (copy_sizes[k]) e = cudaMemcpy(base + off[k], src[k], copy_sizes[k], cudaMemcpyHostToDevice);
+    SynthCatalog hc;
+    hc.nsrc = n;
+    hc.N = N;
+    hc.bins_per_row = bpr;
+    hc.noise_sigma = cat->noise_sigma;
+    hc.x = reinterpret_cast<const int *>(base + off[0]);
+    hc.y = reinterpret_cast<const int *>(base + off[1]);
+    hc.half = reinterpret_cast<const int *>(base + off[2]);
+    hc.profile_off = reinterpret_cast<const int *>(base + off[3]);
+    hc.flux = reinterpret_cast<const float *>(base + off[4]);
+    hc.profile = reinterpret_cast<const float *>(base + off[5]);
+    hc.bin_start = reinterpret_cast<const int *>(base + off[6]);
+    hc.bin_src = reinterpret_cast<const int *>(base + off[7]);
+    ref.d_cat = reinterpret_cast<SynthCatalog *>(base + off[8]);
+    if (e == cudaSuccess) e = cudaMemcpy(ref.d_cat, &hc, sizeof hc, cudaMemcpyHostToDevice);
+    // render the first epoch: one job, no drops
+    SynthJob j;
+    std::memset(&j, 0, sizeof j);
+    j.cat = ref.d_cat;
+    j.out = ref.d_image;
+    j.seed = seed;
+    j.N = N;
+    j.add_src = -1;
+    long long hdr[2] = {1, (long long)(N / kSynthBlock) * (N / kSynthBlock)};
+    void *tmp = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, sizeof j + 16);
+    if (e == cudaSuccess) e = cudaMemcpy(tmp, &j, sizeof j, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(static_cast<char *>(tmp) + sizeof j, hdr, 16, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = launch_synth((int)srv->cfg.dtype, static_cast<SynthJob *>(tmp),
+                         reinterpret_cast<long long *>(static_cast<char *>(tmp) + sizeof j),
+                         srv->synth_grid, ctx->s_comp);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->s_comp);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reference upload");
+    return IQA_OK;
+}
+
+iqa_status check_catalog(iqa_ctx *ctx, const iqa_catalog *c)
+{
+    if (!c || c->N < 16 || c->N % kSynthBlock || c->nsrc < 0 || c->nprofile < 0 ||
+        (c->nsrc > 0 && (!c->x || !c->y || !c->flux || !c->half || !c->profile_off ||
+                         !c->profile))) {
+        set_error(ctx, "bad catalogue (N a multiple of 16, arrays for nsrc sources)");
+        return IQA_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < c->nsrc; ++i) {
+        if (c->half[i] < 0 || c->half[i] > 64 || c->profile_off[i] < 0 ||
+            c->profile_off[i] + 2 * c->half[i] + 1 > c->nprofile || c->x[i] < 0 ||
+            c->x[i] >= c->N || c->y[i] < 0 || c->y[i] >= c->N) {
+            set_error(ctx, "catalogue source %d out of range", i);
+            return IQA_ERR_INVALID_ARG;
+        }
+    }
+    return IQA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+iqa_status iqa_server_create(iqa_ctx *ctx, const iqa_server_config *cfg, iqa_server **out)
+{
+    if (!out || !cfg) return IQA_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!cfg->simulate && !ctx) return IQA_ERR_INVALID_ARG;
+    if (!dtype_ok(cfg->dtype) || cfg->max_pairs_per_step < 1 || cfg->max_pairs_per_step > 64 ||
+        cfg->max_inflight_steps < 1 || cfg->max_inflight_steps > 4 || cfg->pool_bytes < 256 ||
+        cfg->simulate < 0 || cfg->simulate > 2 || !(cfg->step_timeout_ms >= 0)) {
+        set_error(ctx, "bad server config (max_pairs_per_step 1..64, max_inflight_steps "
+                       "1..4, pool_bytes > 0)");
+        return IQA_ERR_INVALID_ARG;
+    }
+    iqa_params P;
+    iqa_status s = resolve_params(ctx, &cfg->params, &P);
+    if (s != IQA_OK) return s;
+    auto srv = std::make_unique<iqa_server>();
+    srv->ctx = ctx;
+    srv->cfg = *cfg;
+    srv->P = P;
+    srv->kcfg = default_batch_config();
+    srv->es = elem_size(cfg->dtype);
+    srv->step_timeout_ms = cfg->step_timeout_ms > 0 ? cfg->step_timeout_ms : 10000.0;
+    srv->pool.reset(cfg->pool_bytes);
+    srv->slots.resize(cfg->max_inflight_steps);
+    if (!cfg->simulate) {
+        {
+            std::lock_guard<std::mutex> g(ctx->cfg_mu);
+            if (ctx->has_batch_cfg[cfg->dtype]) srv->kcfg = ctx->batch_cfg[cfg->dtype];
+        }
+        srv->device = ctx->device;
+        srv->synth_grid = ctx->num_sms * 4;
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaSetDevice(ctx->device);
+        if (ctx->budget && cfg->pool_bytes > ctx->budget) {
+            cudaSetDevice(prev);
+            set_error(ctx, "pool of %zu bytes exceeds the context's HBM budget",
+                      cfg->pool_bytes);
+            return IQA_ERR_NOMEM;
+        }
+        cudaError_t e = cudaMalloc(&srv->d_pool, cfg->pool_bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaSetDevice(prev);
+            set_error(ctx, "pool of %zu bytes: %s", cfg->pool_bytes, cudaGetErrorString(e));
+            return IQA_ERR_NOMEM;
+        }
+        for (auto &sl : srv->slots) {
+            e = alloc_slot(srv.get(), sl);
+            if (e != cudaSuccess) break;
+        }
+        cudaSetDevice(prev);
+        if (e != cudaSuccess) {
+            iqa_server *raw = srv.release();
+            iqa_server_destroy(raw);
+            return cuda_fail(ctx, e, "server step buffers");
+        }
+    }
+    iqa_server *raw = srv.release();
+    raw->worker = std::thread(worker_main, raw);
+    *out = raw;
+    return IQA_OK;
+}
+
+iqa_status iqa_server_add_reference(iqa_server *srv, int ref_id, const iqa_catalog *cat,
+                                    unsigned long long seed)
+{
+    if (!srv) return IQA_ERR_INVALID_ARG;
+    iqa_status s = check_catalog(srv->ctx, cat);
+    if (s != IQA_OK) return s;
+    {
+        std::lock_guard<std::mutex> g(srv->mu);
+        if (srv->refs.count(ref_id)) {
+            set_error(srv->ctx, "reference %d already added", ref_id);
+            return IQA_ERR_INVALID_ARG;
+        }
+    }
+    Reference ref;
+    ref.N = cat->N;
+    ref.nsrc = cat->nsrc;
+    if (!srv->cfg.simulate) {
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaSetDevice(srv->device);
+        s = upload_reference(srv, ref, cat, seed);
+        cudaSetDevice(prev);
+        if (s != IQA_OK) {
+            cudaFree(ref.d_arrays);
+            cudaFree(ref.d_image);
+            return s;
+        }
+    }
+    std::lock_guard<std::mutex> g(srv->mu);
+    srv->refs[ref_id] = ref;
+    return IQA_OK;
+}
+
+iqa_status iqa_server_reference_image(iqa_server *srv, int ref_id, void *host_out)
+{
+    if (!srv || !host_out || srv->cfg.simulate) return IQA_ERR_INVALID_ARG;
+    Reference ref;
+    {
+        std::lock_guard<std::mutex> g(srv->mu);
+        auto it = srv->refs.find(ref_id);
+        if (it == srv->refs.end()) {
+            set_error(srv->ctx, "unknown reference %d", ref_id);
+            return IQA_ERR_INVALID_ARG;
+        }
+        ref = it->second;
+    }
+    cudaError_t e = cudaMemcpy(host_out, ref.d_image, (size_t)ref.N * ref.N * srv->es,
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(srv->ctx, e, "reference read-back");
+    return IQA_OK;
+}
+
+iqa_status iqa_submit(iqa_server *srv, const iqa_request *req, iqa_handle *out)
+{
+    if (!srv || !req || !out) return IQA_ERR_INVALID_ARG;
+    auto r = std::make_shared<Request>();
+    r->r = *req;
+    r->t_submit = Clock::now();
+    std::lock_guard<std::mutex> g(srv->mu);
+    auto it = srv->refs.find(req->ref_id);
+    if (it == srv->refs.end()) {
+        set_error(srv->ctx, "unknown reference %d", req->ref_id);
+        return IQA_ERR_INVALID_ARG;
+    }
+    const int N = it->second.N;
+    const int V = 16 / srv->es;
+    if (req->NT < 1 || N % req->NT || req->NT % V || req->NT > 256 || req->ndrop < 0 ||
+        req->ndrop > kSynthMaxDrop) {
+        set_error(srv->ctx, "bad request: NT must divide N=%d, be a multiple of 16 bytes and "
+                            "<= 256; at most %d drops", N, kSynthMaxDrop);
+        return IQA_ERR_INVALID_ARG;
+    }
+    if (req->add_src >= 0) {
+        // the transient borrows an existing source's profile
+        if (req->add_src >= it->second.nsrc || req->add_x < 0 || req->add_x >= N ||
+            req->add_y < 0 || req->add_y >= N) {
+            set_error(srv->ctx, "transient: source index or centre out of range");
+            return IQA_ERR_INVALID_ARG;
+        }
+    }
+    r->N = N;
+    r->T = N / req->NT;
+    r->epoch_bytes = (size_t)N * N * srv->es;
+    if (round_up(r->epoch_bytes, 256) > srv->pool.size()) {
+        set_error(srv->ctx, "request needs %zu bytes, more than the pool of %zu",
+                  r->epoch_bytes, srv->pool.size());
+        return IQA_ERR_NOMEM;
+    }
+    if (srv->pending.size() >= kMaxQueue) {
+        set_error(srv->ctx, "queue full");
+        return IQA_ERR_BUSY;
+    }
+    r->h = srv->next_handle++;
+    if (!srv->have_first) {
+        srv->have_first = true;
+        srv->t_first = r->t_submit;
+    }
+    ++srv->submitted;
+    srv->pending.push_back(r);
+    srv->all[r->h] = r;
+    *out = r->h;
+    srv->cv_work.notify_one();
+    return IQA_OK;
+}
+
+iqa_status iqa_poll(iqa_server *srv, iqa_handle h, int timeout_us)
+{
+    if (!srv) return IQA_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->all.find(h);
+    if (it == srv->all.end()) {
+        set_error(srv->ctx, "unknown handle %llu", h);
+        return IQA_ERR_INVALID_ARG;
+    }
+    auto r = it->second;
+    auto ready = [&] { return r->state == REQ_DONE || r->state == REQ_FAILED; };
+    if (!ready() && timeout_us > 0)
+        srv->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
+    if (!ready()) return IQA_PENDING;
+    if (r->state == REQ_FAILED && srv->ctx) {
+        std::lock_guard<std::mutex> g(srv->ctx->err_mu);
+        srv->ctx->last_error = r->status == IQA_ERR_TIMEOUT
+                                   ? "request's step ran out of time (device or host watchdog)"
+                                   : "request's step failed: " + srv->worker_error;
+    }
+    return r->status;
+}
+
+iqa_status iqa_result(iqa_server *srv, iqa_handle h, float *lisi_map, float *aug_map,
+                      double *latency_ms)
+{
+    if (!srv) return IQA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(srv->mu);
+    auto it = srv->all.find(h);
+    if (it == srv->all.end()) {
+        set_error(srv->ctx, "unknown handle %llu", h);
+        return IQA_ERR_INVALID_ARG;
+    }
+    auto r = it->second;
+    if (r->state == REQ_PENDING || r->state == REQ_INFLIGHT) return IQA_PENDING;
+    if (r->state == REQ_FAILED) {
+        srv->all.erase(it);
+        return r->status;
+    }
+    const size_t n = (size_t)r->T * r->T;
+    if (lisi_map) std::memcpy(lisi_map, r->lisi.data(), n * sizeof(float));
+    if (aug_map) std::memcpy(aug_map, r->aug.data(), n * sizeof(float));
+    if (latency_ms) *latency_ms = ms_between(r->t_submit, r->t_done);
+    srv->all.erase(it);
+    return IQA_OK;
+}
+
+iqa_status iqa_server_get_stats(iqa_server *srv, iqa_server_stats *out)
+{
+    if (!srv || !out) return IQA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(srv->mu);
+    std::memset(out, 0, sizeof *out);
+    out->submitted = srv->submitted;
+    out->completed = srv->completed;
+    out->failed = srv->failed;
+    out->pending = (long long)srv->pending.size();
+    long long inflight = 0;
+    for (auto &s : srv->slots)
+        if (s.busy) inflight += (long long)s.reqs.size();
+    out->inflight = inflight;
+    out->steps = srv->steps;
+    out->mean_pairs_per_step = srv->steps ? (double)srv->step_pairs / srv->steps : 0.0;
+    out->pool_bytes = srv->pool.size();
+    out->pool_peak_bytes = srv->pool.peak();
+    if (!srv->latencies.empty()) {
+        std::vector<double> v = srv->latencies;
+        std::sort(v.begin(), v.end());
+        auto q = [&](double p) {
+            size_t i = (size_t)std::min<double>(v.size() - 1, std::ceil(p * v.size()) - 1);
+            return v[i];
+        };
+        out->p50_ms = q(0.50);
+        out->p99_ms = q(0.99);
+        out->max_ms = v.back();
+        double sum = 0.0;
+        for (double x : v) sum += x;
+        out->mean_ms = sum / v.size();
+        const double span_s = ms_between(srv->t_first, srv->t_last) / 1e3;
+        if (span_s > 0) {
+            out->pairs_per_s = srv->completed / span_s;
+            out->input_gb_per_s = srv->bytes_done / span_s / 1e9;
+        }
+    }
+    return IQA_OK;
+}
+
+void iqa_server_destroy(iqa_server *srv)
+{
+    if (!srv) return;
+    {
+        std::lock_guard<std::mutex> g(srv->mu);
+        srv->stop = true;
+        // a stalled simulated step would never end: let the worker leave
+        if (srv->cfg.simulate == 2)
+            for (auto &s : srv->slots) s.busy = false;
+    }
+    srv->cv_work.notify_all();
+    if (srv->worker.joinable()) srv->worker.join();
+    if (!srv->cfg.simulate) {
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaSetDevice(srv->device);
+        for (auto &s : srv->slots) {
+            if (s.st) cudaStreamSynchronize(s.st);
+            free_slot(s);
+        }
+        for (auto &kv : srv->refs) {
+            cudaFree(kv.second.d_arrays);
+            cudaFree(kv.second.d_image);
+        }
+        cudaFree(srv->d_pool);
+        cudaSetDevice(prev);
+    }
+    delete srv;
+}
+
+}  // extern "C"

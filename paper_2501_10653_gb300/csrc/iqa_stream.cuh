@@ -62,6 +62,9 @@ struct StreamParams {
     unsigned long long *sched;
     int inject_stall;        // test hook: 1 = the producer issues nothing
     int pad2_;
+    // nullable: {npairs, total_units} in device memory, read at launch in
+    // place of the two fields above (a captured graph replayed with new work)
+    const long long *dyn;
     PairDesc one_pair;
 };
 
@@ -133,6 +136,16 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// A tensor map in a global-memory table may have been rewritten since the TMA
+// unit last read that address (a plan's re-upload, a server step, a no-alloc
+// call): acquire the new contents for the tensor-map proxy before first use.
+__device__ __forceinline__ void acquire_tmap(const CUtensorMap *map)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                     reinterpret_cast<uint64_t>(map))
+                 : "memory");
+}
+
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map)
 {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
@@ -190,6 +203,8 @@ __global__ void __launch_bounds__(CT + 32, 1)
     int *abort_flag = reinterpret_cast<int *>(part + kMaxTX * 4);
 
     const PairDesc *descs = sp.descs ? sp.descs : &sp.one_pair;
+    const int npairs = sp.dyn ? (int)sp.dyn[0] : sp.npairs;
+    const long long total_units = sp.dyn ? sp.dyn[1] : sp.total_units;
     const int tid = threadIdx.x;
     const bool producer = tid >= CT;
 
@@ -215,12 +230,12 @@ __global__ void __launch_bounds__(CT + 32, 1)
         while (ok) {
             // the next unit's index is fetched before this unit's copies are
             // issued, so the atomic's latency hides behind them
-            if (u < sp.total_units) {
+            if (u < total_units) {
                 if (sp.sched) u_next = (long long)atomicAdd(&sp.sched[0], 1ull);
                 else u_next = blockIdx.x + (++i) * (long long)gridDim.x;
             }
-            const bool last = u >= sp.total_units;
-            const int pi = (!last && sp.npairs > 1) ? find_pair(descs, sp.npairs, u) : 0;
+            const bool last = u >= total_units;
+            const int pi = (!last && npairs > 1) ? find_pair(descs, npairs, u) : 0;
             const PairDesc &d = descs[pi];
             const int nchunks = last ? 1 : d.chunks;
             long long lu = 0;
@@ -228,6 +243,10 @@ __global__ void __launch_bounds__(CT + 32, 1)
             uint32_t bytes = 0;
             if (!last) {
                 if (pi != last_pair) {
+                    if (sp.descs) {
+                        acquire_tmap(&d.tmx);
+                        acquire_tmap(&d.tmy);
+                    }
                     prefetch_tmap(&d.tmx);
                     prefetch_tmap(&d.tmy);
                     last_pair = pi;
@@ -304,7 +323,7 @@ __global__ void __launch_bounds__(CT + 32, 1)
             // a new unit: its descriptor fields are read once into registers
             u = stage_unit[s];
             if (u < 0) return;
-            d = &descs[sp.npairs > 1 ? find_pair(descs, sp.npairs, u) : 0];
+            d = &descs[npairs > 1 ? find_pair(descs, npairs, u) : 0];
             lu = u - d->unit_begin;
             V = d->CH * d->LPU;
             chunks = d->chunks;

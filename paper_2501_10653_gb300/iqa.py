@@ -77,6 +77,44 @@ class iqa_host_pair(ctypes.Structure):
                 ("aug_map", ctypes.c_void_p), ("sums", ctypes.c_void_p)]
 
 
+class iqa_catalog(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("nsrc", ctypes.c_int),
+                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("flux", ctypes.c_void_p),
+                ("half", ctypes.c_void_p), ("profile_off", ctypes.c_void_p),
+                ("profile", ctypes.c_void_p), ("nprofile", ctypes.c_int),
+                ("noise_sigma", ctypes.c_float)]
+
+
+class iqa_server_config(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("max_pairs_per_step", ctypes.c_int),
+                ("max_inflight_steps", ctypes.c_int), ("pool_bytes", ctypes.c_size_t),
+                ("one_pair_per_launch", ctypes.c_int), ("simulate", ctypes.c_int),
+                ("sim_bytes_per_s", ctypes.c_double), ("step_timeout_ms", ctypes.c_double),
+                ("params", iqa_params)]
+
+
+class iqa_request(ctypes.Structure):
+    _fields_ = [("ref_id", ctypes.c_int), ("NT", ctypes.c_int),
+                ("seed", ctypes.c_ulonglong), ("ndrop", ctypes.c_int),
+                ("drop", ctypes.c_int * 8), ("add_src", ctypes.c_int),
+                ("add_x", ctypes.c_int), ("add_y", ctypes.c_int),
+                ("add_flux", ctypes.c_float)]
+
+
+class iqa_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("failed", ctypes.c_longlong), ("pending", ctypes.c_longlong),
+                ("inflight", ctypes.c_longlong), ("steps", ctypes.c_longlong),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("pairs_per_s", ctypes.c_double), ("input_gb_per_s", ctypes.c_double),
+                ("mean_pairs_per_step", ctypes.c_double),
+                ("pool_bytes", ctypes.c_ulonglong), ("pool_peak_bytes", ctypes.c_ulonglong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class iqa_plan_stats(ctypes.Structure):
     _fields_ = [("npairs", ctypes.c_int), ("total_units", ctypes.c_longlong),
                 ("grid", ctypes.c_int), ("input_bytes", ctypes.c_ulonglong),
@@ -124,6 +162,14 @@ def _declare(lib):
         "iqa_batch_noalloc": ([P(iqa_pair), _i, _i, P(iqa_params), _vp], _st),
         "iqa_merge": ([_vp, _vp, _i, _i, P(iqa_params), _vp, _vp, _vp, _vp], _st),
         "iqa_both_host_many": ([_vp, P(iqa_host_pair), _i, _i, P(iqa_params)], _st),
+        "iqa_server_create": ([_vp, P(iqa_server_config), P(_vp)], _st),
+        "iqa_server_add_reference": ([_vp, _i, P(iqa_catalog), ctypes.c_ulonglong], _st),
+        "iqa_server_reference_image": ([_vp, _i, _vp], _st),
+        "iqa_submit": ([_vp, P(iqa_request), P(ctypes.c_ulonglong)], _st),
+        "iqa_poll": ([_vp, ctypes.c_ulonglong, _i], _st),
+        "iqa_result": ([_vp, ctypes.c_ulonglong, _vp, _vp, P(ctypes.c_double)], _st),
+        "iqa_server_get_stats": ([_vp, P(iqa_server_stats)], _st),
+        "iqa_server_destroy": ([_vp], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -333,3 +379,88 @@ def iqa_both_host_many(ctx, pairs, dtype, params=None):
     arr = (iqa_host_pair * len(pairs))(*pairs)
     return _check(ctx, lib().iqa_both_host_many(ctx, arr, len(pairs), int(dtype),
                                                 _params(params)))
+
+
+# --- serving loop --------------------------------------------------------------
+
+class _Server:
+    """Owner of an iqa_server handle (and of the context it reports errors on)."""
+
+    def __init__(self, ctx, handle):
+        self.ctx = ctx
+        self.handle = handle
+
+
+def iqa_server_create(ctx, dtype=IQA_F16, max_pairs_per_step=16, max_inflight_steps=2,
+                      pool_bytes=8 << 30, one_pair_per_launch=0, simulate=0,
+                      sim_bytes_per_s=1e12, step_timeout_ms=0.0, params=None):
+    p = iqa_params(1e-6, 1e-6, 1e-6, 0.0) if params is None else params
+    if isinstance(p, dict):
+        p = iqa_params(p.get("C1", 1e-6), p.get("C2", 1e-6), p.get("C", 1e-6), p.get("D", 0.0))
+    cfg = iqa_server_config(int(dtype), int(max_pairs_per_step), int(max_inflight_steps),
+                            int(pool_bytes), int(one_pair_per_launch), int(simulate),
+                            float(sim_bytes_per_s), float(step_timeout_ms), p)
+    h = _vp()
+    _check(ctx, lib().iqa_server_create(ctx, ctypes.byref(cfg), ctypes.byref(h)))
+    return _Server(ctx, h.value)
+
+
+def iqa_server_add_reference(srv, ref_id, cat, seed):
+    """cat: a dict as made by synth.serving_catalog (numpy arrays)."""
+    import numpy as np
+    arrs = {k: np.ascontiguousarray(cat[k], dtype=np.int32 if k in ("x", "y", "half",
+                                                                      "profile_off")
+                                    else np.float32)
+            for k in ("x", "y", "half", "profile_off", "flux", "profile")}
+    c = iqa_catalog(int(cat["N"]), len(arrs["x"]), arrs["x"].ctypes.data,
+                    arrs["y"].ctypes.data, arrs["flux"].ctypes.data, arrs["half"].ctypes.data,
+                    arrs["profile_off"].ctypes.data, arrs["profile"].ctypes.data,
+                    len(arrs["profile"]), float(cat["noise_sigma"]))
+    return _check(srv.ctx, lib().iqa_server_add_reference(srv.handle, int(ref_id),
+                                                          ctypes.byref(c), int(seed)))
+
+
+def iqa_server_reference_image(srv, ref_id, host_out):
+    return _check(srv.ctx, lib().iqa_server_reference_image(srv.handle, int(ref_id),
+                                                            _ptr(host_out)))
+
+
+def make_request(ref_id, NT, seed, drop=(), add=None):
+    """An iqa_request; more than 8 drops are passed on as such (the library
+    rejects them)."""
+    d = [int(v) for v in drop]
+    head = d[:8]
+    arr = (ctypes.c_int * 8)(*(head + [-1] * (8 - len(head))))
+    a = add if add is not None else (-1, 0, 0, 0.0)
+    return iqa_request(int(ref_id), int(NT), int(seed), len(d), arr, int(a[0]), int(a[1]),
+                       int(a[2]), float(a[3]))
+
+
+def iqa_submit(srv, req):
+    h = ctypes.c_ulonglong()
+    _check(srv.ctx, lib().iqa_submit(srv.handle, ctypes.byref(req), ctypes.byref(h)))
+    return h.value
+
+
+def iqa_poll(srv, h, timeout_us=0):
+    """Returns the status (IQA_OK, IQA_PENDING or an error code); no raise."""
+    return lib().iqa_poll(srv.handle, int(h), int(timeout_us))
+
+
+def iqa_result(srv, h, lisi_map=None, aug_map=None):
+    lat = ctypes.c_double()
+    _check(srv.ctx, lib().iqa_result(srv.handle, int(h), _ptr(lisi_map), _ptr(aug_map),
+                                     ctypes.byref(lat)))
+    return lat.value
+
+
+def iqa_server_get_stats(srv):
+    st = iqa_server_stats()
+    _check(srv.ctx, lib().iqa_server_get_stats(srv.handle, ctypes.byref(st)))
+    return st
+
+
+def iqa_server_destroy(srv):
+    if srv.handle:
+        lib().iqa_server_destroy(srv.handle)
+        srv.handle = None

@@ -171,3 +171,101 @@ def precision_pair(i, N=8192, seed=3, dtype="f32"):
     drops the faintest 10%.  Returns FP64-derived images in ``dtype``."""
     return sky_pair(N, n_src=33, flux=(1e-4, 1.0), fwhm=4.0, noise=5e-3,
                     n_drop=4, ext_frac=0.5, seed=seed, pair_index=i, dtype=dtype)
+
+
+# --- device-reproducible epochs (the serving workload) -----------------------
+#
+# The serving loop renders epochs on the device (csrc/iqa_synth.cu).  The
+# functions below make the same images on the host, bit for bit, so that tests
+# can feed the oracle inputs that never came from the CUDA path:
+#   * noise: Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11), key = seed,
+#     counter = (pixel low word, pixel high word, 0x5EED, 0); four 16-bit
+#     uniforms (w >> 16) * 2^-16 summed, minus 2, times sqrt(3) (Irwin-Hall of
+#     four: unit variance, bounded at +-sqrt(12));
+#   * sources: integer centres, float32 1-D profiles g[-h..h]; contribution
+#     (f * g[dy]) * g[dx], added to the pixel in catalogue order;
+#   * pixel = sky + sigma * z in float32, rounded to nearest into storage.
+
+_PHILOX_M0 = np.uint64(0xD2511F53)
+_PHILOX_M1 = np.uint64(0xCD9E8D57)
+_PHILOX_W0 = 0x9E3779B9
+_PHILOX_W1 = 0xBB67AE85
+_MASK32 = np.uint64(0xFFFFFFFF)
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Vectorised Philox4x32-10 over uint32 counter arrays; returns 4 words."""
+    c0, c1, c2, c3 = (np.asarray(v, dtype=np.uint64) & _MASK32 for v in (c0, c1, c2, c3))
+    k0 = int(k0) & 0xFFFFFFFF
+    k1 = int(k1) & 0xFFFFFFFF
+    for _ in range(10):
+        p0 = _PHILOX_M0 * c0
+        p1 = _PHILOX_M1 * c2
+        hi0, lo0 = p0 >> np.uint64(32), p0 & _MASK32
+        hi1, lo1 = p1 >> np.uint64(32), p1 & _MASK32
+        c0, c1, c2, c3 = (hi1 ^ c1 ^ np.uint64(k0)), lo1, (hi0 ^ c3 ^ np.uint64(k1)), lo0
+        k0 = (k0 + _PHILOX_W0) & 0xFFFFFFFF
+        k1 = (k1 + _PHILOX_W1) & 0xFFFFFFFF
+    return c0, c1, c2, c3
+
+
+def epoch_noise(N, seed):
+    """float32 N x N standardised noise z of the device generator."""
+    pix = np.arange(N * N, dtype=np.uint64)
+    w = philox4x32_10(pix & _MASK32, pix >> np.uint64(32), np.uint64(0x5EED),
+                      np.uint64(0), seed & 0xFFFFFFFF, seed >> 32)
+    scale = np.float32(1.0 / 65536.0)
+    s = (w[0] >> np.uint64(16)).astype(np.float32) * scale
+    for k in (1, 2, 3):
+        s = s + (w[k] >> np.uint64(16)).astype(np.float32) * scale
+    return ((s + np.float32(-2.0)) * np.float32(1.7320508075688772)).reshape(N, N)
+
+
+def serving_catalog(N, ref_index, seed=4, fwhm=4.0, flux=(0.005, 2.0), noise=2e-4):
+    """A reference sky of the serving workload: round(33 (N/2048)^2) Gaussian-beam
+    sources at integer centres, flux log-uniform, with float32 profiles."""
+    rng = np.random.default_rng([seed, 5, ref_index])
+    n_src = max(1, int(round(33 * (N / 2048.0) ** 2)))
+    sig = fwhm * FWHM_TO_SIGMA
+    h = int(math.ceil(6.0 * sig))
+    k = np.arange(-h, h + 1, dtype=np.float64)
+    prof = np.exp(-(k * k) / (2.0 * sig * sig)).astype(np.float32)
+    return {
+        "N": N,
+        "x": rng.integers(0, N, n_src).astype(np.int32),
+        "y": rng.integers(0, N, n_src).astype(np.int32),
+        "flux": np.exp(rng.uniform(math.log(flux[0]), math.log(flux[1]), n_src)
+                       ).astype(np.float32),
+        "half": np.full(n_src, h, dtype=np.int32),
+        "profile_off": (np.arange(n_src, dtype=np.int32) * (2 * h + 1)),
+        "profile": np.tile(prof, n_src),
+        "noise_sigma": np.float32(noise),
+    }
+
+
+def render_epoch(cat, seed, drop=(), add=None, dtype="f32"):
+    """Host mirror of the device epoch generator.  add = (src, x, y, flux) puts
+    a transient with source `src`'s profile at (x, y)."""
+    N = cat["N"]
+    sky = np.zeros((N, N), dtype=np.float32)
+    drop = set(int(d) for d in drop)
+
+    def put(i, cx, cy, f):
+        h = int(cat["half"][i])
+        g = cat["profile"][cat["profile_off"][i]:cat["profile_off"][i] + 2 * h + 1]
+        r0, r1 = max(0, cy - h), min(N, cy + h + 1)
+        c0, c1 = max(0, cx - h), min(N, cx + h + 1)
+        if r0 >= r1 or c0 >= c1:
+            return
+        gy = np.float32(f) * g[r0 - cy + h:r1 - cy + h]
+        gx = g[c0 - cx + h:c1 - cx + h]
+        sky[r0:r1, c0:c1] = sky[r0:r1, c0:c1] + gy[:, None] * gx[None, :]
+
+    for i in range(len(cat["x"])):
+        if i in drop:
+            continue
+        put(i, int(cat["x"][i]), int(cat["y"][i]), cat["flux"][i])
+    if add is not None:
+        put(int(add[0]), int(add[1]), int(add[2]), np.float32(add[3]))
+    img = sky + np.float32(cat["noise_sigma"]) * epoch_noise(N, seed)
+    return _cast(img.astype(np.float32), dtype) if dtype != "f32" else img

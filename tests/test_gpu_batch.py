@@ -178,3 +178,23 @@ def test_device_wait_timeout_reports_and_context_recovers(ctx, orc):
         x, y = b.host[i]
         parity.assert_parity(b.results(i), parity.oracle_maps(orc, x, y, NT, PARAMS),
                              PARAMS)
+
+
+def test_rewritten_descriptor_tables_are_reread(ctx, orc):
+    """Plans created one after another reuse the same device table addresses
+    with new tensor maps; each launch must read the new maps (the kernel
+    acquires every table-resident tensor map before first use)."""
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    sets = [Batch([(512, 64), (1024, 32)], seed=31), Batch([(1024, 128), (256, 16)], seed=32),
+            Batch([(768, 96), (512, 32)], seed=33)]
+    for rep in range(2):
+        for b in sets:
+            for t in b.out:
+                for u in t:
+                    u.fill_(float("nan"))
+            _run(ctx, b, flags=rep)
+            for i, (N, NT) in enumerate(b.specs):
+                x, y = b.host[i]
+                parity.assert_parity(b.results(i), parity.oracle_maps(orc, x, y, NT, PARAMS),
+                                     PARAMS)

@@ -77,14 +77,16 @@ def test_noalloc_matches_existing_entry_point_on_two_calls_in_a_row(lib_ctx):
     torch.cuda.synchronize()
     _check_against_reference(lib_ctx, first)
     _check_against_reference(lib_ctx, second)
-    # the same pairs again: the shared array is reused, counters start at zero
-    for it in first:
-        it["l"].fill_(float("nan"))
-        it["a"].fill_(float("nan"))
-        it["s"].fill_(float("nan"))
-    iqa.iqa_batch_noalloc(pairs1, iqa.IQA_F32, PARAMS, st)
-    torch.cuda.synchronize()
-    _check_against_reference(lib_ctx, first)
+    # alternating calls rewrite the same array entries with other pairs: every
+    # call must see its own descriptors, and the counters start at zero
+    for batch, pairs in ((first, pairs1), (second, pairs2), (first, pairs1)):
+        for it in batch:
+            it["l"].fill_(float("nan"))
+            it["a"].fill_(float("nan"))
+            it["s"].fill_(float("nan"))
+        iqa.iqa_batch_noalloc(pairs, iqa.IQA_F32, PARAMS, st)
+        torch.cuda.synchronize()
+        _check_against_reference(lib_ctx, batch)
 
 
 def test_noalloc_rejects_more_pairs_than_its_array_holds(lib_ctx):
