@@ -76,6 +76,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the N=8192 FP32/FP16/BF16 precision and throughput report")
+    ap.add_argument("--serve-seconds", type=float, default=5.0,
+                    help="length of the served Poisson trace (0: skip serving)")
     ap.add_argument("--precision-batch", type=int, default=16,
                     help="N=8192 pairs per launch in the precision throughput report")
     ap.add_argument("--tune-iters", type=int, default=3,
@@ -342,6 +344,71 @@ def precision_report(iqa, ctx, params, stream, batch=16):
     return out
 
 
+SERVE_NS = (512, 1024, 2048, 4096, 8192, 16384)
+
+
+def serving_report(iqa, ctx, seconds, rate=2000.0, n_refs=32, seed=4):
+    """The serving workload: Poisson arrivals (rate per s, for `seconds`) of
+    requests against n_refs resident reference skies (N uniform over
+    512..16384, FP16), N_T uniform over {32, 64, 128}, each second epoch
+    rendered on the device from its seed (2 sources dropped, a transient in
+    half of them).  Served by the continuous-batching server, then by the
+    one-pair-per-launch FP32 baseline on the same trace; plus a saturation
+    burst for the maximum pairs/s of each."""
+    from paper_2501_10653_gb300 import synth
+    rng = np.random.default_rng([seed, 9])
+    cats = {i: synth.serving_catalog(SERVE_NS[i % len(SERVE_NS)], i, seed=seed)
+            for i in range(n_refs)}
+    n = int(rate * seconds)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
+    trace = []
+    for i in range(n):
+        rid = int(rng.integers(n_refs))
+        cat = cats[rid]
+        nsrc = len(cat["x"])
+        drop = [int(v) for v in rng.choice(nsrc, size=min(2, nsrc), replace=False)]
+        add = None
+        if rng.random() < 0.5:
+            N = cat["N"]
+            add = (int(rng.integers(nsrc)), int(rng.integers(N)), int(rng.integers(N)),
+                   float(np.exp(rng.uniform(np.log(0.01), 0.0))))
+        trace.append(iqa.make_request(rid, int(rng.choice([32, 64, 128])), 10**9 + i,
+                                      drop, add))
+
+    def run(dtype, one_pair, timed, burst=None):
+        srv = iqa.iqa_server_create(ctx, dtype=dtype, max_pairs_per_step=32,
+                                    max_inflight_steps=4, pool_bytes=8 << 30,
+                                    one_pair_per_launch=one_pair,
+                                    max_step_bytes=256 << 20, params=PARAMS)
+        try:
+            for rid, cat in cats.items():
+                iqa.iqa_server_add_reference(srv, rid, cat, 7 + rid)
+            reqs = trace if burst is None else trace[:burst]
+            times = arrivals[:len(reqs)] if timed else np.zeros(len(reqs))
+            t0 = time.perf_counter()
+            iqa.iqa_server_run_trace(srv, reqs, times, timeout_s=600.0)
+            wall = time.perf_counter() - t0
+            st = iqa.iqa_server_get_stats(srv).as_dict()
+            st["wall_s"] = round(wall, 3)
+            return {k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()}
+        finally:
+            iqa.iqa_server_destroy(srv)
+
+    burst = min(n, 2000)
+    out = {
+        "workload": "Poisson %.0f req/s for %.1f s (%d requests); %d resident FP16 reference "
+                    "skies, N uniform over %s; N_T in {32,64,128}; epoch 2 rendered on the "
+                    "device (2 sources dropped, a transient in half)" % (
+                        rate, seconds, n, n_refs, list(SERVE_NS)),
+        "served": run(iqa.IQA_F16, 0, True),
+        "baseline_one_pair_per_launch_f32": run(iqa.IQA_F32, 1, True),
+        "saturation_burst": burst,
+        "served_saturation": run(iqa.IQA_F16, 0, False, burst),
+        "baseline_saturation": run(iqa.IQA_F32, 1, False, burst),
+    }
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -445,6 +512,9 @@ def run_ours(args):
     prec = None
     if rank == 0 and world == 1 and not args.no_precision:
         prec = precision_report(iqa, ctx, params, stream, args.precision_batch)
+    serve = None
+    if rank == 0 and world == 1 and args.serve_seconds > 0:
+        serve = serving_report(iqa, ctx, args.serve_seconds)
 
     # end to end through the host-buffer entry point: one call per step over
     # the same B pairs in page-locked host memory, uploads pipelined with the
@@ -531,6 +601,7 @@ def run_ours(args):
                                    % info["config"]["threads"]},
             "cpu_baseline": cpu,
             "precision_N8192": prec,
+            "serving": serve,
             "paper_context": PAPER_H100,
         }
     iqa.iqa_plan_destroy(plan)

@@ -389,7 +389,7 @@ typedef unsigned long long iqa_handle;
  * pixel at offset (dy, dx) from its centre.  All arrays are host memory and
  * are copied. */
 typedef struct {
-    int N;                  /* image side, a multiple of 16 */
+    int N;                  /* image side, a multiple of 64 */
     int nsrc;
     const int *x;           /* source centres, columns */
     const int *y;           /* source centres, rows */
@@ -400,6 +400,7 @@ typedef struct {
     int nprofile;           /* floats in `profile` */
     float noise_sigma;      /* sigma of each epoch's noise */
 } iqa_catalog;
+/* (at most 64 sources' windows may meet any 64 x 64 block of the image) */
 
 typedef struct {
     iqa_dtype dtype;           /* storage of references and epochs */
@@ -416,6 +417,10 @@ typedef struct {
     double step_timeout_ms;    /* host watchdog: a step still running after this
                                   fails its requests with IQA_ERR_TIMEOUT (its
                                   buffers stay reserved until it ends); 0 = 10 s */
+    unsigned long long max_step_bytes; /* cap on a step's input bytes (2 N^2 per
+                                  pair; a larger request still runs alone), so a
+                                  large request does not hold small ones back;
+                                  0 = no cap */
     iqa_params params;
 } iqa_server_config;
 
@@ -471,6 +476,17 @@ iqa_status iqa_result(iqa_server *srv, iqa_handle h, float *lisi_map, float *aug
                       double *latency_ms);
 
 iqa_status iqa_server_get_stats(iqa_server *srv, iqa_server_stats *out);
+
+/*
+ * Load generator (a simulated imaging cadence): submits reqs[i] at arrival_s[i]
+ * seconds after the call, timing each arrival on a steady clock in the calling
+ * thread, then waits up to timeout_s for every one of them to finish.  The
+ * maps of these requests are dropped when they finish; the latency statistics
+ * (iqa_server_get_stats) keep them.  Returns IQA_OK, IQA_ERR_TIMEOUT (not all
+ * finished in time), or the first iqa_submit error.
+ */
+iqa_status iqa_server_run_trace(iqa_server *srv, const iqa_request *reqs,
+                                const double *arrival_s, int n, double timeout_s);
 
 /* Stops the worker after the steps in flight, frees everything. */
 void iqa_server_destroy(iqa_server *srv);

@@ -115,6 +115,7 @@ struct Request {
     size_t epoch_bytes = 0, pool_off = 0;
     ReqState state = REQ_PENDING;
     iqa_status status = IQA_PENDING;
+    bool discard = false;  // drop the maps (and the record) when finished
     Clock::time_point t_submit, t_done;
     std::vector<float> lisi, aug;
 };
@@ -136,8 +137,11 @@ struct Slot {
     int *d_status = nullptr, *h_status = nullptr;
     float *d_out = nullptr, *h_out = nullptr;
     size_t out_cap = 0;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    // one graph per grid size: a step launches the smallest persistent grid
+    // that covers its units, so small steps leave SMs to concurrent steps
+    cudaGraph_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};
+    int grid[4] = {0, 0, 0, 0};
 };
 
 }  // namespace
@@ -180,8 +184,10 @@ const size_t kMaxQueue = 1 << 20;
 
 void free_slot(Slot &s)
 {
-    if (s.exec) cudaGraphExecDestroy(s.exec);
-    if (s.graph) cudaGraphDestroy(s.graph);
+    for (int g = 0; g < 4; ++g) {
+        if (s.exec[g]) cudaGraphExecDestroy(s.exec[g]);
+        if (s.graph[g]) cudaGraphDestroy(s.graph[g]);
+    }
     cudaFree(s.d_jobs);
     cudaFree(s.d_synth_hdr);
     cudaFree(s.d_pairs);
@@ -215,33 +221,43 @@ StreamParams slot_stream_params(const iqa_server *srv, const Slot &s)
     return sp;
 }
 
-// The slot's graph: work-table uploads, the epoch generator and the
-// persistent map kernel, all sized from device-side headers.
+// The slot's graphs: work-table uploads, the epoch generator and the
+// persistent map kernel, all sized from device-side headers; graph g runs the
+// kernels on (g+1)/8, 2/8, 4/8 or all of the full persistent grid.
 cudaError_t capture_slot(iqa_server *srv, Slot &s)
 {
     const int M = srv->cfg.max_pairs_per_step;
-    cudaError_t e = cudaStreamBeginCapture(s.st, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return e;
-    cudaError_t e1 = cudaMemcpyAsync(s.d_jobs, s.h_jobs, sizeof(SynthJob) * M,
-                                     cudaMemcpyHostToDevice, s.st);
-    if (e1 == cudaSuccess)
-        e1 = cudaMemcpyAsync(s.d_synth_hdr, s.h_synth_hdr, 16, cudaMemcpyHostToDevice, s.st);
-    if (e1 == cudaSuccess)
-        e1 = cudaMemcpyAsync(s.d_pairs, s.h_pairs, sizeof(PairDesc) * M,
-                             cudaMemcpyHostToDevice, s.st);
-    if (e1 == cudaSuccess)
-        e1 = cudaMemcpyAsync(s.d_dyn, s.h_dyn, 16, cudaMemcpyHostToDevice, s.st);
-    if (e1 == cudaSuccess)
-        e1 = launch_synth((int)srv->cfg.dtype, s.d_jobs, s.d_synth_hdr, srv->synth_grid, s.st);
-    if (e1 == cudaSuccess) {
-        StreamParams sp = slot_stream_params(srv, s);
-        const int grid = srv->ctx->num_sms * srv->kcfg.ctas_per_sm;
-        e1 = launch_stream(sp, srv->cfg.dtype, srv->kcfg, MAPS_AB, grid, s.st);
+    const int full = srv->ctx->num_sms * srv->kcfg.ctas_per_sm;
+    const int div[4] = {8, 4, 2, 1};
+    for (int g = 0; g < 4; ++g) {
+        const int grid = std::max(1, full / div[g]);
+        const int sgrid = std::max(1, srv->synth_grid / div[g]);
+        s.grid[g] = grid;
+        cudaError_t e = cudaStreamBeginCapture(s.st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        cudaError_t e1 = cudaMemcpyAsync(s.d_jobs, s.h_jobs, sizeof(SynthJob) * M,
+                                         cudaMemcpyHostToDevice, s.st);
+        if (e1 == cudaSuccess)
+            e1 = cudaMemcpyAsync(s.d_synth_hdr, s.h_synth_hdr, 16, cudaMemcpyHostToDevice,
+                                 s.st);
+        if (e1 == cudaSuccess)
+            e1 = cudaMemcpyAsync(s.d_pairs, s.h_pairs, sizeof(PairDesc) * M,
+                                 cudaMemcpyHostToDevice, s.st);
+        if (e1 == cudaSuccess)
+            e1 = cudaMemcpyAsync(s.d_dyn, s.h_dyn, 16, cudaMemcpyHostToDevice, s.st);
+        if (e1 == cudaSuccess)
+            e1 = launch_synth((int)srv->cfg.dtype, s.d_jobs, s.d_synth_hdr, sgrid, s.st);
+        if (e1 == cudaSuccess) {
+            StreamParams sp = slot_stream_params(srv, s);
+            e1 = launch_stream(sp, srv->cfg.dtype, srv->kcfg, MAPS_AB, grid, s.st);
+        }
+        e = cudaStreamEndCapture(s.st, &s.graph[g]);
+        if (e1 != cudaSuccess) return e1;
+        if (e != cudaSuccess) return e;
+        e = cudaGraphInstantiate(&s.exec[g], s.graph[g], 0);
+        if (e != cudaSuccess) return e;
     }
-    e = cudaStreamEndCapture(s.st, &s.graph);
-    if (e1 != cudaSuccess) return e1;
-    if (e != cudaSuccess) return e;
-    return cudaGraphInstantiate(&s.exec, s.graph, 0);
+    return cudaSuccess;
 }
 
 cudaError_t alloc_slot(iqa_server *srv, Slot &s)
@@ -341,7 +357,7 @@ iqa_status launch_step(iqa_server *srv, Slot &s)
         j.add_x = r.r.add_x;
         j.add_y = r.r.add_y;
         j.add_flux = r.r.add_flux;
-        blocks += (long long)(r.N / kSynthBlock) * (r.N / kSynthBlock);
+        blocks += (long long)(r.N / kSynthBin) * (r.N / kSynthBin);
         float *dl = s.d_out + o, *da = s.d_out + o + (size_t)r.T * r.T;
         o += 2 * (size_t)r.T * r.T;
         if (srv->cfg.one_pair_per_launch) continue;
@@ -381,7 +397,9 @@ iqa_status launch_step(iqa_server *srv, Slot &s)
             }
         }
     } else {
-        e = cudaGraphLaunch(s.exec, s.st);
+        int g = 0;
+        while (g < 3 && s.grid[g] < units) ++g;
+        e = cudaGraphLaunch(s.exec[g], s.st);
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s.h_out, s.d_out, floats * sizeof(float), cudaMemcpyDeviceToHost,
@@ -440,7 +458,10 @@ void retire(iqa_server *srv, Slot &s)
             s.timed_out = true;
             const auto now = Clock::now();
             for (auto &r : s.reqs)
-                if (r->state == REQ_INFLIGHT) finish_request(srv, *r, IQA_ERR_TIMEOUT, now);
+                if (r->state == REQ_INFLIGHT) {
+                    finish_request(srv, *r, IQA_ERR_TIMEOUT, now);
+                    if (r->discard) srv->all.erase(r->h);
+                }
             srv->cv_done.notify_all();
         }
         return;
@@ -451,7 +472,9 @@ void retire(iqa_server *srv, Slot &s)
         Request &r = *rp;
         const size_t n = (size_t)r.T * r.T;
         if (r.state == REQ_INFLIGHT) {
-            if (st == IQA_OK && !srv->cfg.simulate) {
+            if (r.discard) {
+                // nothing kept
+            } else if (st == IQA_OK && !srv->cfg.simulate) {
                 r.lisi.assign(s.h_out + o, s.h_out + o + n);
                 r.aug.assign(s.h_out + o + n, s.h_out + o + 2 * n);
             } else if (st == IQA_OK) {
@@ -460,6 +483,7 @@ void retire(iqa_server *srv, Slot &s)
             }
             finish_request(srv, r, st, now);
         }
+        if (r.discard) srv->all.erase(r.h);
         o += 2 * n;
         srv->pool.release(r.pool_off, r.epoch_bytes);
     }
@@ -490,10 +514,16 @@ void worker_main(iqa_server *srv)
         if (!srv->stop && free_slot_p && !srv->pending.empty()) {
             Slot &s = *free_slot_p;
             const int cap = srv->cfg.one_pair_per_launch ? 1 : srv->cfg.max_pairs_per_step;
+            unsigned long long step_bytes = 0;
             while ((int)s.reqs.size() < cap && !srv->pending.empty()) {
                 auto r = srv->pending.front();
+                const unsigned long long rb = 2ull * r->epoch_bytes;
+                if (srv->cfg.max_step_bytes && !s.reqs.empty() &&
+                    step_bytes + rb > srv->cfg.max_step_bytes)
+                    break;
                 size_t off = 0;
                 if (!srv->pool.alloc(r->epoch_bytes, &off)) break;  // arrival order kept
+                step_bytes += rb;
                 r->pool_off = off;
                 r->state = REQ_INFLIGHT;
                 srv->pending.pop_front();
@@ -510,6 +540,7 @@ void worker_main(iqa_server *srv)
                     for (auto &r : s.reqs) {
                         finish_request(srv, *r, st, now);
                         srv->pool.release(r->pool_off, r->epoch_bytes);
+                        if (r->discard) srv->all.erase(r->h);
                     }
                     srv->worker_error = iqa_last_error(srv->ctx);
                     s.reqs.clear();
@@ -543,6 +574,11 @@ iqa_status upload_reference(iqa_server *srv, Reference &ref, const iqa_catalog *
         for (int br = r0; br <= r1; ++br)
             for (int bc = c0; bc <= c1; ++bc) bins[(size_t)br * bpr + bc].push_back(i);
     }
+    for (const auto &bl : bins)
+        if (bl.size() > 64) {
+            set_error(ctx, "a 64x64 bin meets %zu sources (at most 64)", bl.size());
+            return IQA_ERR_INVALID_ARG;
+        }
     std::vector<int> start(bins.size() + 1, 0), flat;
     for (size_t b = 0; b < bins.size(); ++b) {
         start[b + 1] = start[b] + (int)bins[b].size();
@@ -604,7 +640,7 @@ iqa_status upload_reference(iqa_server *srv, Reference &ref, const iqa_catalog *
     j.seed = seed;
     j.N = N;
     j.add_src = -1;
-    long long hdr[2] = {1, (long long)(N / kSynthBlock) * (N / kSynthBlock)};
+    long long hdr[2] = {1, (long long)(N / kSynthBin) * (N / kSynthBin)};
     void *tmp = nullptr;
     if (e == cudaSuccess) e = cudaMalloc(&tmp, sizeof j + 16);
     if (e == cudaSuccess) e = cudaMemcpy(tmp, &j, sizeof j, cudaMemcpyHostToDevice);
@@ -622,10 +658,10 @@ iqa_status upload_reference(iqa_server *srv, Reference &ref, const iqa_catalog *
 
 iqa_status check_catalog(iqa_ctx *ctx, const iqa_catalog *c)
 {
-    if (!c || c->N < 16 || c->N % kSynthBlock || c->nsrc < 0 || c->nprofile < 0 ||
+    if (!c || c->N < kSynthBin || c->N % kSynthBin || c->nsrc < 0 || c->nprofile < 0 ||
         (c->nsrc > 0 && (!c->x || !c->y || !c->flux || !c->half || !c->profile_off ||
                          !c->profile))) {
-        set_error(ctx, "bad catalogue (N a multiple of 16, arrays for nsrc sources)");
+        set_error(ctx, "bad catalogue (N a multiple of 64, arrays for nsrc sources)");
         return IQA_ERR_INVALID_ARG;
     }
     for (int i = 0; i < c->nsrc; ++i) {
@@ -759,11 +795,13 @@ iqa_status iqa_server_reference_image(iqa_server *srv, int ref_id, void *host_ou
     return IQA_OK;
 }
 
-iqa_status iqa_submit(iqa_server *srv, const iqa_request *req, iqa_handle *out)
+static iqa_status submit_impl(iqa_server *srv, const iqa_request *req, iqa_handle *out,
+                              bool discard)
 {
     if (!srv || !req || !out) return IQA_ERR_INVALID_ARG;
     auto r = std::make_shared<Request>();
     r->r = *req;
+    r->discard = discard;
     r->t_submit = Clock::now();
     std::lock_guard<std::mutex> g(srv->mu);
     auto it = srv->refs.find(req->ref_id);
@@ -809,6 +847,43 @@ iqa_status iqa_submit(iqa_server *srv, const iqa_request *req, iqa_handle *out)
     srv->all[r->h] = r;
     *out = r->h;
     srv->cv_work.notify_one();
+    return IQA_OK;
+}
+
+iqa_status iqa_submit(iqa_server *srv, const iqa_request *req, iqa_handle *out)
+{
+    return submit_impl(srv, req, out, false);
+}
+
+iqa_status iqa_server_run_trace(iqa_server *srv, const iqa_request *reqs,
+                                const double *arrival_s, int n, double timeout_s)
+{
+    if (!srv || !reqs || !arrival_s || n < 0) return IQA_ERR_INVALID_ARG;
+    long long base_done;
+    {
+        std::lock_guard<std::mutex> g(srv->mu);
+        base_done = srv->completed + srv->failed;
+    }
+    const auto t0 = Clock::now();
+    for (int i = 0; i < n; ++i) {
+        const auto due = t0 + std::chrono::duration_cast<Clock::duration>(
+                                  std::chrono::duration<double>(arrival_s[i]));
+        while (Clock::now() < due) {
+        }
+        iqa_handle h;
+        iqa_status s = submit_impl(srv, &reqs[i], &h, true);
+        if (s != IQA_OK) return s;
+    }
+    std::unique_lock<std::mutex> lk(srv->mu);
+    const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                             std::chrono::duration<double>(timeout_s));
+    const bool ok = srv->cv_done.wait_until(lk, deadline, [&] {
+        return srv->completed + srv->failed - base_done >= n;
+    });
+    if (!ok) {
+        set_error(srv->ctx, "trace not finished after %.1f s", timeout_s);
+        return IQA_ERR_TIMEOUT;
+    }
     return IQA_OK;
 }
 

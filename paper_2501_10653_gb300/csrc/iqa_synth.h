@@ -6,8 +6,8 @@
 
 namespace iqa {
 
-constexpr int kSynthBlock = 16;   // pixels per side of a generator block
-constexpr int kSynthBin = 64;     // pixels per side of a catalogue bin
+constexpr int kSynthBin = 64;     // pixels per side of a catalogue bin and of
+                                  // a generator work unit
 constexpr int kSynthMaxDrop = 8;  // sources a request may drop
 
 // A reference catalogue in device memory.
@@ -30,7 +30,7 @@ struct SynthCatalog {
 struct SynthJob {
     const SynthCatalog *cat;     // device pointer
     void *out;                   // N*N storage elements
-    long long blocks_begin;      // first generator block of this job
+    long long blocks_begin;      // first catalogue bin (work unit) of this job
     unsigned long long seed;
     int N;
     int ndrop;
@@ -40,8 +40,9 @@ struct SynthJob {
     float add_flux;              // transient peak flux
 };
 
-// Renders every job of the table; header = {njobs, total_blocks} in device
-// memory (so a captured graph can replay it with new contents).
+// Renders every job of the table (at most 64); header = {njobs, total_bins}
+// in device memory (so a captured graph can replay it with new contents).
+// N must be a multiple of kSynthBin, and a bin may list at most 64 sources.
 cudaError_t launch_synth(int dtype, const SynthJob *jobs, const long long *header, int grid,
                          cudaStream_t st);
 

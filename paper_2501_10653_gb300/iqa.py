@@ -90,7 +90,7 @@ class iqa_server_config(ctypes.Structure):
                 ("max_inflight_steps", ctypes.c_int), ("pool_bytes", ctypes.c_size_t),
                 ("one_pair_per_launch", ctypes.c_int), ("simulate", ctypes.c_int),
                 ("sim_bytes_per_s", ctypes.c_double), ("step_timeout_ms", ctypes.c_double),
-                ("params", iqa_params)]
+                ("max_step_bytes", ctypes.c_ulonglong), ("params", iqa_params)]
 
 
 class iqa_request(ctypes.Structure):
@@ -170,6 +170,8 @@ def _declare(lib):
         "iqa_result": ([_vp, ctypes.c_ulonglong, _vp, _vp, P(ctypes.c_double)], _st),
         "iqa_server_get_stats": ([_vp, P(iqa_server_stats)], _st),
         "iqa_server_destroy": ([_vp], None),
+        "iqa_server_run_trace": ([_vp, P(iqa_request), P(ctypes.c_double), _i,
+                                  ctypes.c_double], _st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -393,13 +395,15 @@ class _Server:
 
 def iqa_server_create(ctx, dtype=IQA_F16, max_pairs_per_step=16, max_inflight_steps=2,
                       pool_bytes=8 << 30, one_pair_per_launch=0, simulate=0,
-                      sim_bytes_per_s=1e12, step_timeout_ms=0.0, params=None):
+                      sim_bytes_per_s=1e12, step_timeout_ms=0.0, max_step_bytes=0,
+                      params=None):
     p = iqa_params(1e-6, 1e-6, 1e-6, 0.0) if params is None else params
     if isinstance(p, dict):
         p = iqa_params(p.get("C1", 1e-6), p.get("C2", 1e-6), p.get("C", 1e-6), p.get("D", 0.0))
     cfg = iqa_server_config(int(dtype), int(max_pairs_per_step), int(max_inflight_steps),
                             int(pool_bytes), int(one_pair_per_launch), int(simulate),
-                            float(sim_bytes_per_s), float(step_timeout_ms), p)
+                            float(sim_bytes_per_s), float(step_timeout_ms),
+                            int(max_step_bytes), p)
     h = _vp()
     _check(ctx, lib().iqa_server_create(ctx, ctypes.byref(cfg), ctypes.byref(h)))
     return _Server(ctx, h.value)
@@ -464,3 +468,11 @@ def iqa_server_destroy(srv):
     if srv.handle:
         lib().iqa_server_destroy(srv.handle)
         srv.handle = None
+
+
+def iqa_server_run_trace(srv, reqs, arrival_s, timeout_s=600.0):
+    """Native load generator: submits reqs[i] at arrival_s[i] s, waits for all."""
+    arr = (iqa_request * len(reqs))(*reqs)
+    t = (ctypes.c_double * len(reqs))(*[float(v) for v in arrival_s])
+    return _check(srv.ctx, lib().iqa_server_run_trace(srv.handle, arr, t, len(reqs),
+                                                      float(timeout_s)))

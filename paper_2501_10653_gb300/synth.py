@@ -179,8 +179,9 @@ def precision_pair(i, N=8192, seed=3, dtype="f32"):
 # functions below make the same images on the host, bit for bit, so that tests
 # can feed the oracle inputs that never came from the CUDA path:
 #   * noise: Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11), key = seed,
-#     counter = (pixel low word, pixel high word, 0x5EED, 0); four 16-bit
-#     uniforms (w >> 16) * 2^-16 summed, minus 2, times sqrt(3) (Irwin-Hall of
+#     counter = (q low word, q high word, 0x5EED, 0) with q = pixel index / 2;
+#     words 0-1 give the even pixel's four 16-bit uniforms, words 2-3 the odd
+#     pixel's; their sum times 2^-16, minus 2, times sqrt(3) (Irwin-Hall of
 #     four: unit variance, bounded at +-sqrt(12));
 #   * sources: integer centres, float32 1-D profiles g[-h..h]; contribution
 #     (f * g[dy]) * g[dx], added to the pixel in catalogue order;
@@ -210,15 +211,26 @@ def philox4x32_10(c0, c1, c2, c3, k0, k1):
 
 
 def epoch_noise(N, seed):
-    """float32 N x N standardised noise z of the device generator."""
-    pix = np.arange(N * N, dtype=np.uint64)
-    w = philox4x32_10(pix & _MASK32, pix >> np.uint64(32), np.uint64(0x5EED),
+    """float32 N x N standardised noise z of the device generator: one Philox
+    call per pair of horizontally adjacent pixels (q = pixel index / 2), words
+    0-1 for the even pixel and 2-3 for the odd one, each word split into two
+    16-bit uniforms (high half first)."""
+    q = np.arange(N * N // 2, dtype=np.uint64)
+    w = philox4x32_10(q & _MASK32, q >> np.uint64(32), np.uint64(0x5EED),
                       np.uint64(0), seed & 0xFFFFFFFF, seed >> 32)
     scale = np.float32(1.0 / 65536.0)
-    s = (w[0] >> np.uint64(16)).astype(np.float32) * scale
-    for k in (1, 2, 3):
-        s = s + (w[k] >> np.uint64(16)).astype(np.float32) * scale
-    return ((s + np.float32(-2.0)) * np.float32(1.7320508075688772)).reshape(N, N)
+
+    def ih4(a, b):
+        s = (a >> np.uint64(16)).astype(np.float32) * scale
+        s = s + (a & np.uint64(0xFFFF)).astype(np.float32) * scale
+        s = s + (b >> np.uint64(16)).astype(np.float32) * scale
+        s = s + (b & np.uint64(0xFFFF)).astype(np.float32) * scale
+        return (s + np.float32(-2.0)) * np.float32(1.7320508075688772)
+
+    z = np.empty(N * N, dtype=np.float32)
+    z[0::2] = ih4(w[0], w[1])
+    z[1::2] = ih4(w[2], w[3])
+    return z.reshape(N, N)
 
 
 def serving_catalog(N, ref_index, seed=4, fwhm=4.0, flux=(0.005, 2.0), noise=2e-4):

@@ -150,3 +150,35 @@ def test_bad_requests_and_config(lib):
         iqa.iqa_server_create(None, max_pairs_per_step=65, simulate=1)
     with pytest.raises(iqa.IqaError):
         iqa.iqa_server_create(None, simulate=0)
+
+
+def test_step_byte_cap_splits_large_from_small(lib):
+    """With a cap of 4 MB of input per step, a 2048^2 FP16 pair (16 MB) runs
+    alone and the 512^2 pairs (1 MB each) are grouped up to four per step."""
+    srv = _server(lib, max_pairs_per_step=16, max_step_bytes=4 << 20, sim_bytes_per_s=2e9)
+    try:
+        hs = [iqa.iqa_submit(srv, iqa.make_request(2, 64, 0))]
+        hs += [iqa.iqa_submit(srv, iqa.make_request(0, 64, i)) for i in range(16)]
+        _wait_all(srv, hs)
+        st = iqa.iqa_server_get_stats(srv)
+        assert st.completed == 17
+        assert st.steps >= 5  # 1 large + at least 4 groups of <= 4 small
+    finally:
+        iqa.iqa_server_destroy(srv)
+
+
+def test_native_trace_driver(lib):
+    """iqa_server_run_trace submits at the given times and returns when all have
+    finished; the statistics count every request and the wall time covers the
+    trace."""
+    srv = _server(lib, sim_bytes_per_s=50e9)
+    try:
+        reqs = [iqa.make_request(i % 3, 64, i) for i in range(100)]
+        times = [0.002 * i for i in range(100)]
+        t0 = time.time()
+        iqa.iqa_server_run_trace(srv, reqs, times, 30.0)
+        assert time.time() - t0 >= 0.198
+        st = iqa.iqa_server_get_stats(srv)
+        assert st.completed == 100 and st.pending == 0 and st.p99_ms > 0
+    finally:
+        iqa.iqa_server_destroy(srv)
