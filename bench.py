@@ -76,6 +76,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the N=8192 FP32/FP16/BF16 precision and throughput report")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the 64-pair mixed-size batch report")
     ap.add_argument("--serve-seconds", type=float, default=5.0,
                     help="length of the served Poisson trace (0: skip serving)")
     ap.add_argument("--precision-batch", type=int, default=16,
@@ -347,6 +349,63 @@ def precision_report(iqa, ctx, params, stream, batch=16):
 SERVE_NS = (512, 1024, 2048, 4096, 8192, 16384)
 
 
+def mixed_batch_report(iqa, ctx, params, stream, K=10):
+    """The batched workload: 64 pairs, N from {1024, 2048, 4096, 8192}
+    (weights 4:3:2:1), N_T from {32, 64, 128}, FP32; each pair a seeded sky of
+    round(33 (N/2048)^2) Gaussian-beam sources (integer centres) over 2e-4
+    noise, epoch 2 without the faintest 10% and with fresh noise, rendered on
+    the device.  One persistent launch over all 64 (graph, autotuned) against
+    one iqa_both launch per pair."""
+    import math
+    import torch
+    from paper_2501_10653_gb300 import synth
+    specs = synth.mixed_batch_specs()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    xs, ys, outs, pairs = [], [], [], []
+    total = 0
+    for i, (N, NT) in enumerate(specs):
+        cat = synth.serving_catalog(N, i, seed=2)
+        cat2 = synth.catalog_without_faintest(cat, int(math.ceil(0.1 * len(cat["x"]))))
+        x = torch.empty(N * N, device=dev)
+        y = torch.empty(N * N, device=dev)
+        iqa.iqa_render_epoch(ctx, cat, 2 * 10**6 + 2 * i, x, iqa.IQA_F32)
+        iqa.iqa_render_epoch(ctx, cat2, 2 * 10**6 + 2 * i + 1, y, iqa.IQA_F32)
+        T = N // NT
+        o = (torch.empty(T * T, device=dev), torch.empty(T * T, device=dev))
+        xs.append(x)
+        ys.append(y)
+        outs.append(o)
+        pairs.append(iqa.make_pair(x, y, N, NT, *o))
+        total += 2 * N * N * 4
+    plan = iqa.iqa_plan_create(ctx, pairs, iqa.IQA_F32, params, iqa.IQA_PLAN_GRAPH)
+    tuned = iqa.iqa_plan_autotune(plan, stream, 2).as_dict()
+    ms = _time_plan(iqa, ctx, plan, stream, K, 2)
+    iqa.iqa_plan_destroy(plan)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for (N, NT), x, y, o in zip(specs, xs, ys, outs):
+            iqa.iqa_both(ctx, x, y, iqa.IQA_F32, N, NT, params, o[0], o[1], None, stream)
+        e0.record(stream)
+        for _ in range(K):
+            for (N, NT), x, y, o in zip(specs, xs, ys, outs):
+                iqa.iqa_both(ctx, x, y, iqa.IQA_F32, N, NT, params, o[0], o[1], None, stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    per_pair_ms = e0.elapsed_time(e1)
+    out = {"workload": "64 pairs, N in {1024,2048,4096,8192} (4:3:2:1), N_T in {32,64,128}, "
+                       "FP32, skies rendered on the device", "input_bytes": total,
+           "one_launch_us": round(ms * 1e3 / K, 1),
+           "one_launch_GBs": round(K * total / (ms * 1e-3) / 1e9, 1),
+           "one_launch_pairs_per_s": round(K * 64 / (ms * 1e-3), 1),
+           "per_pair_launches_GBs": round(K * total / (per_pair_ms * 1e-3) / 1e9, 1),
+           "per_pair_launches_pairs_per_s": round(K * 64 / (per_pair_ms * 1e-3), 1),
+           "tuned": tuned}
+    del xs, ys, outs
+    torch.cuda.empty_cache()
+    return out
+
+
 def serving_report(iqa, ctx, seconds, rate=2000.0, n_refs=32, seed=4):
     """The serving workload: Poisson arrivals (rate per s, for `seconds`) of
     requests against n_refs resident reference skies (N uniform over
@@ -512,6 +571,9 @@ def run_ours(args):
     prec = None
     if rank == 0 and world == 1 and not args.no_precision:
         prec = precision_report(iqa, ctx, params, stream, args.precision_batch)
+    mixed = None
+    if rank == 0 and world == 1 and not args.no_mixed:
+        mixed = mixed_batch_report(iqa, ctx, params, stream)
     serve = None
     if rank == 0 and world == 1 and args.serve_seconds > 0:
         serve = serving_report(iqa, ctx, args.serve_seconds)
@@ -600,6 +662,7 @@ def run_ours(args):
                          "kernel": "iqa_stream_kernel<float,%d,1,1> (persistent, TMA)"
                                    % info["config"]["threads"]},
             "cpu_baseline": cpu,
+            "mixed_batch_64": mixed,
             "precision_N8192": prec,
             "serving": serve,
             "paper_context": PAPER_H100,

@@ -456,6 +456,22 @@ iqa_status iqa_server_create(iqa_ctx *ctx, const iqa_server_config *cfg,
 iqa_status iqa_server_add_reference(iqa_server *srv, int ref_id, const iqa_catalog *cat,
                                     unsigned long long seed);
 
+/*
+ * The serving loop's sky generator as a call of its own: renders one epoch of
+ * `cat` on the device -- its sources minus drop[0..ndrop), plus a transient
+ * with source add_src's profile at (add_x, add_y) and peak add_flux when
+ * add_src >= 0, over noise from `seed` -- rounded to nearest into `dtype` at
+ * `out` (device, N*N elements).  The catalogue is uploaded for the call and
+ * freed after it; the call waits for the render to finish.  The recipe (a
+ * counter-based Philox4x32-10 noise draw, sources in catalogue order) is
+ * reproducible on the host bit for bit.
+ * Errors: IQA_ERR_INVALID_ARG (bad catalogue, drop list or transient),
+ * IQA_ERR_NOMEM, IQA_ERR_CUDA.
+ */
+iqa_status iqa_render_epoch(iqa_ctx *ctx, const iqa_catalog *cat, unsigned long long seed,
+                            const int *drop, int ndrop, int add_src, int add_x, int add_y,
+                            float add_flux, iqa_dtype dtype, void *out);
+
 /* Copies a resident reference image (N*N storage elements) to host memory. */
 iqa_status iqa_server_reference_image(iqa_server *srv, int ref_id, void *host_out);
 

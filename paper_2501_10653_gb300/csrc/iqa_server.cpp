@@ -557,10 +557,11 @@ void worker_main(iqa_server *srv)
     }
 }
 
-iqa_status upload_reference(iqa_server *srv, Reference &ref, const iqa_catalog *cat,
-                            unsigned long long seed)
+// Copies a catalogue and its 64x64 bin lists to one device allocation
+// (*d_arrays), with the SynthCatalog struct at its end (*d_cat).
+iqa_status upload_catalog(iqa_ctx *ctx, const iqa_catalog *cat, void **d_arrays,
+                          SynthCatalog **d_cat)
 {
-    iqa_ctx *ctx = srv->ctx;
     const int N = cat->N, n = cat->nsrc;
     const int bpr = (N + kSynthBin - 1) / kSynthBin;
     // catalogue bins: every source whose window meets a bin, in catalogue order
@@ -598,16 +599,14 @@ iqa_status upload_reference(iqa_server *srv, Reference &ref, const iqa_catalog *
     }
     off[8] = total;
     total += round_up(sizeof(SynthCatalog), 256);
-    const size_t img_bytes = (size_t)N * N * srv->es;
-    cudaError_t e = cudaMalloc(&ref.d_arrays, total);
-    if (e == cudaSuccess) e = cudaMalloc(&ref.d_image, img_bytes);
+    cudaError_t e = cudaMalloc(d_arrays, total);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        set_error(ctx, "reference of %zu bytes does not fit: %s", img_bytes + total,
-                  cudaGetErrorString(e));
+        *d_arrays = nullptr;
+        set_error(ctx, "catalogue of %zu bytes does not fit: %s", total, cudaGetErrorString(e));
         return IQA_ERR_NOMEM;
     }
-    char *base = static_cast<char *>(ref.d_arrays);
+    char *base = static_cast<char *>(*d_arrays);
     const void *src[8] = {cat->x, cat->y, cat->half, cat->profile_off, cat->flux,
                           cat->profile, start.data(), flat.data()};
     const size_t copy_sizes[8] = {sizeof(int) * (size_t)n, sizeof(int) * (size_t)n,
@@ -616,7 +615,8 @@ iqa_status upload_reference(iqa_server *srv, Reference &ref, const iqa_catalog *
                                   sizeof(float) * (size_t)cat->nprofile,
                                   sizeof(int) * start.size(), sizeof(int) * flat.size()};
     for (int k = 0; k < 8 && e == cudaSuccess; ++k)
-        if (copy_sizes[k]) e = cudaMemcpy(base + off[k], src[k], copy_sizes[k], cudaMemcpyHostToDevice);
+        if (copy_sizes[k])
+            e = cudaMemcpy(base + off[k], src[k], copy_sizes[k], cudaMemcpyHostToDevice);
     SynthCatalog hc;
     hc.nsrc = n;
     hc.N = N;
@@ -630,30 +630,62 @@ iqa_status upload_reference(iqa_server *srv, Reference &ref, const iqa_catalog *
     hc.profile = reinterpret_cast<const float *>(base + off[5]);
     hc.bin_start = reinterpret_cast<const int *>(base + off[6]);
     hc.bin_src = reinterpret_cast<const int *>(base + off[7]);
-    ref.d_cat = reinterpret_cast<SynthCatalog *>(base + off[8]);
-    if (e == cudaSuccess) e = cudaMemcpy(ref.d_cat, &hc, sizeof hc, cudaMemcpyHostToDevice);
-    // render the first epoch: one job, no drops
+    *d_cat = reinterpret_cast<SynthCatalog *>(base + off[8]);
+    if (e == cudaSuccess) e = cudaMemcpy(*d_cat, &hc, sizeof hc, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "catalogue upload");
+    return IQA_OK;
+}
+
+// Renders one epoch of an uploaded catalogue into `out` and waits for it.
+iqa_status render_one(iqa_ctx *ctx, SynthCatalog *d_cat, int N, unsigned long long seed,
+                      const int *drop, int ndrop, int add_src, int add_x, int add_y,
+                      float add_flux, iqa_dtype dtype, void *out, cudaStream_t st)
+{
     SynthJob j;
     std::memset(&j, 0, sizeof j);
-    j.cat = ref.d_cat;
-    j.out = ref.d_image;
+    j.cat = d_cat;
+    j.out = out;
     j.seed = seed;
     j.N = N;
-    j.add_src = -1;
+    j.ndrop = ndrop;
+    for (int k = 0; k < ndrop; ++k) j.drop[k] = drop[k];
+    j.add_src = add_src;
+    j.add_x = add_x;
+    j.add_y = add_y;
+    j.add_flux = add_flux;
     long long hdr[2] = {1, (long long)(N / kSynthBin) * (N / kSynthBin)};
     void *tmp = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc(&tmp, sizeof j + 16);
+    cudaError_t e = cudaMalloc(&tmp, sizeof j + 16);
     if (e == cudaSuccess) e = cudaMemcpy(tmp, &j, sizeof j, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(static_cast<char *>(tmp) + sizeof j, hdr, 16, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = launch_synth((int)srv->cfg.dtype, static_cast<SynthJob *>(tmp),
+        e = launch_synth((int)dtype, static_cast<SynthJob *>(tmp),
                          reinterpret_cast<long long *>(static_cast<char *>(tmp) + sizeof j),
-                         srv->synth_grid, ctx->s_comp);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->s_comp);
+                         ctx->num_sms * 4, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(tmp);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "reference upload");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "epoch render");
     return IQA_OK;
+}
+
+iqa_status upload_reference(iqa_server *srv, Reference &ref, const iqa_catalog *cat,
+                            unsigned long long seed)
+{
+    iqa_ctx *ctx = srv->ctx;
+    iqa_status s = upload_catalog(ctx, cat, &ref.d_arrays, &ref.d_cat);
+    if (s != IQA_OK) return s;
+    const size_t img_bytes = (size_t)cat->N * cat->N * srv->es;
+    cudaError_t e = cudaMalloc(&ref.d_image, img_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ref.d_image = nullptr;
+        set_error(ctx, "reference of %zu bytes does not fit: %s", img_bytes,
+                  cudaGetErrorString(e));
+        return IQA_ERR_NOMEM;
+    }
+    return render_one(ctx, ref.d_cat, cat->N, seed, nullptr, 0, -1, 0, 0, 0.0f,
+                      srv->cfg.dtype, ref.d_image, ctx->s_comp);
 }
 
 iqa_status check_catalog(iqa_ctx *ctx, const iqa_catalog *c)
@@ -774,6 +806,36 @@ iqa_status iqa_server_add_reference(iqa_server *srv, int ref_id, const iqa_catal
     std::lock_guard<std::mutex> g(srv->mu);
     srv->refs[ref_id] = ref;
     return IQA_OK;
+}
+
+iqa_status iqa_render_epoch(iqa_ctx *ctx, const iqa_catalog *cat, unsigned long long seed,
+                            const int *drop, int ndrop, int add_src, int add_x, int add_y,
+                            float add_flux, iqa_dtype dtype, void *out)
+{
+    if (!ctx || !out) return IQA_ERR_INVALID_ARG;
+    if (!dtype_ok(dtype)) {
+        set_error(ctx, "unknown dtype %d", (int)dtype);
+        return IQA_ERR_INVALID_ARG;
+    }
+    iqa_status s = check_catalog(ctx, cat);
+    if (s != IQA_OK) return s;
+    if (ndrop < 0 || ndrop > kSynthMaxDrop || (ndrop && !drop) || add_src >= cat->nsrc ||
+        (add_src >= 0 && (add_x < 0 || add_x >= cat->N || add_y < 0 || add_y >= cat->N))) {
+        set_error(ctx, "bad drop list or transient");
+        return IQA_ERR_INVALID_ARG;
+    }
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+    void *arrays = nullptr;
+    SynthCatalog *d_cat = nullptr;
+    s = upload_catalog(ctx, cat, &arrays, &d_cat);
+    if (s == IQA_OK)
+        s = render_one(ctx, d_cat, cat->N, seed, drop, ndrop, add_src, add_x, add_y, add_flux,
+                       dtype, out, ctx->s_comp);
+    cudaFree(arrays);
+    cudaSetDevice(prev);
+    return s;
 }
 
 iqa_status iqa_server_reference_image(iqa_server *srv, int ref_id, void *host_out)

@@ -172,6 +172,8 @@ def _declare(lib):
         "iqa_server_destroy": ([_vp], None),
         "iqa_server_run_trace": ([_vp, P(iqa_request), P(ctypes.c_double), _i,
                                   ctypes.c_double], _st),
+        "iqa_render_epoch": ([_vp, P(iqa_catalog), ctypes.c_ulonglong, P(_i), _i, _i, _i,
+                              _i, ctypes.c_float, _i, _vp], _st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -409,8 +411,9 @@ def iqa_server_create(ctx, dtype=IQA_F16, max_pairs_per_step=16, max_inflight_st
     return _Server(ctx, h.value)
 
 
-def iqa_server_add_reference(srv, ref_id, cat, seed):
-    """cat: a dict as made by synth.serving_catalog (numpy arrays)."""
+def _catalog(cat):
+    """An iqa_catalog over a dict as made by synth.serving_catalog; returns the
+    struct and the arrays it points into (keep both alive for the call)."""
     import numpy as np
     arrs = {k: np.ascontiguousarray(cat[k], dtype=np.int32 if k in ("x", "y", "half",
                                                                       "profile_off")
@@ -420,8 +423,25 @@ def iqa_server_add_reference(srv, ref_id, cat, seed):
                     arrs["y"].ctypes.data, arrs["flux"].ctypes.data, arrs["half"].ctypes.data,
                     arrs["profile_off"].ctypes.data, arrs["profile"].ctypes.data,
                     len(arrs["profile"]), float(cat["noise_sigma"]))
+    return c, arrs
+
+
+def iqa_server_add_reference(srv, ref_id, cat, seed):
+    """cat: a dict as made by synth.serving_catalog (numpy arrays)."""
+    c, _keep = _catalog(cat)
     return _check(srv.ctx, lib().iqa_server_add_reference(srv.handle, int(ref_id),
                                                           ctypes.byref(c), int(seed)))
+
+
+def iqa_render_epoch(ctx, cat, seed, out, dtype=IQA_F32, drop=(), add=None):
+    """Render one epoch of `cat` on the device into `out` (N*N elements)."""
+    c, _keep = _catalog(cat)
+    d = [int(v) for v in drop]
+    arr = (ctypes.c_int * max(1, len(d)))(*(d or [0]))
+    a = add if add is not None else (-1, 0, 0, 0.0)
+    return _check(ctx, lib().iqa_render_epoch(ctx, ctypes.byref(c), int(seed), arr, len(d),
+                                              int(a[0]), int(a[1]), int(a[2]), float(a[3]),
+                                              int(dtype), _ptr(out)))
 
 
 def iqa_server_reference_image(srv, ref_id, host_out):

@@ -281,3 +281,13 @@ def render_epoch(cat, seed, drop=(), add=None, dtype="f32"):
         put(int(add[0]), int(add[1]), int(add[2]), np.float32(add[3]))
     img = sky + np.float32(cat["noise_sigma"]) * epoch_noise(N, seed)
     return _cast(img.astype(np.float32), dtype) if dtype != "f32" else img
+
+
+def catalog_without_faintest(cat, k):
+    """A serving catalogue with its k lowest-flux sources removed (the second
+    epoch of the batched workload); profiles stay shared."""
+    keep = np.sort(np.argsort(cat["flux"], kind="stable")[k:])
+    out = dict(cat)
+    for key in ("x", "y", "flux", "half", "profile_off"):
+        out[key] = cat[key][keep]
+    return out

@@ -193,3 +193,17 @@ def test_device_stall_is_reported_and_the_context_recovers(ctx, orc):
         parity.assert_parity((l, a, None), parity.oracle_maps(orc, x, y, 64, PARAMS), PARAMS)
     finally:
         iqa.iqa_server_destroy(srv)
+
+
+@pytest.mark.parametrize("dt", ["f32", "f16", "bf16"])
+def test_render_epoch_matches_host_mirror_bitwise(ctx, dt):
+    """The public generator entry point, with drops and a transient."""
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    cat = synth.serving_catalog(1024, 3)
+    out = torch.empty(1024 * 1024, dtype={"f32": torch.float32, "f16": torch.float16,
+                                          "bf16": torch.bfloat16}[dt], device="cuda")
+    iqa.iqa_render_epoch(ctx, cat, 987654321, out, DT[dt], drop=[1, 4], add=(2, 500, 17, 0.3))
+    got = out.cpu().view(torch.int16 if dt != "f32" else torch.int32).numpy()
+    want = synth.render_epoch(cat, 987654321, drop=[1, 4], add=(2, 500, 17, 0.3), dtype=dt)
+    assert np.array_equal(got.view(np.uint8), want.reshape(-1).view(np.uint8))
