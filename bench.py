@@ -54,8 +54,8 @@ PROFILED_TRAFFIC = {
                 "paper_2501_10653_gb300/csrc/iqa_stream.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream_launch.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream_f32.cu"],
-    "sha256": "52dc439a77057917c4d15f88d9b18838d145cfa842110c3c0a7fe79fdbb9da87",
-    "bytes_per_pair": (268486912 + 3892736) / 8,
+    "sha256": "ef33f77a7e2098c1b1f81c9ae8e1f49c3a50b2c99c9369a9705231fa3ac96716",
+    "bytes_per_pair": (268488448 + 3964160) / 8,
     "capture": "8 pairs per launch, scaled by pairs to the timed launch",
 }
 PAPER_H100 = {"lisi_kernel_ms": 0.101, "auglisi_kernel_ms": 0.091,
