@@ -213,13 +213,11 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle as it stands, on the host cores
 
-def cpu_baseline(x, y, seconds):
-    import oracle
-    orc = oracle.Oracle()
-    threads = (os.cpu_count() or 1) if orc.has_openmp else 1
+def _oracle_rate(orc, x, y, seconds, threads):
+    """FP64 oracle throughput (GB/s of FP32 pair bytes) over bands of whole
+    tile rows of one pair, repeated until `seconds` have passed."""
     N = x.shape[0]
     T = N // N_TILE
-    # a bounded sample: bands of whole tile rows, repeated until `seconds`
     rows_per_call = max(1, T // 8)
     done_px, t0, calls = 0, time.perf_counter(), 0
     while True:
@@ -232,11 +230,22 @@ def cpu_baseline(x, y, seconds):
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    gbs = done_px * 8 / el / 1e9
+    return done_px * 8 / el / 1e9, calls, rows_per_call, el
+
+
+def cpu_baseline(x, y, seconds):
+    import oracle
+    orc = oracle.Oracle()
+    threads = (os.cpu_count() or 1) if orc.has_openmp else 1
+    N = x.shape[0]
+    gbs, calls, rows_per_call, el = _oracle_rate(orc, x, y, seconds, threads)
+    one, _, _, el1 = _oracle_rate(orc, x, y, max(1.0, seconds / 4), 1)
     return {"value": round(gbs, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
             "sample": "%d tile-row bands (%d x %d px each) of one N=2048 FP32 pair, "
                       "N_T=64, %.1f s of FP64 oracle work" % (calls, rows_per_call * N_TILE,
                                                              N, el),
+            "single_thread_value": round(one, 4),
+            "single_thread_seconds": round(el1, 1),
             "cpu": _cpu_model()}
 
 
@@ -542,19 +551,31 @@ def run_ours(args):
         p1.record(stream)
     torch.cuda.synchronize()
     per_pair_us = p0.elapsed_time(p1) * 1e3 / (reps * G)
-    single = []
-    for i in range(20):
-        with torch.cuda.stream(stream):
-            torch.cuda._sleep(200000)
-            a0 = torch.cuda.Event(enable_timing=True)
-            a1 = torch.cuda.Event(enable_timing=True)
-            a0.record(stream)
-            iqa.iqa_both(ctx, dx[i % B], dy[i % B], iqa.IQA_F32, N, NT, params,
-                         lisi[i % B], aug[i % B], None, stream)
-            a1.record(stream)
-        torch.cuda.synchronize()
-        single.append(a0.elapsed_time(a1) * 1e3)
-    single_us = float(np.median(single[3:]))
+    def single_launches(fn, count):
+        """Device time of `count` isolated launches (a GPU-side delay queued
+        ahead of each, so the launch is already queued when the events run);
+        successive launches rotate over the B pairs, so a launch's pixels were
+        last touched B - 1 pairs (far more than L2) earlier."""
+        out = []
+        for i in range(count):
+            with torch.cuda.stream(stream):
+                torch.cuda._sleep(200000)
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                fn(i % B)
+                a1.record(stream)
+            torch.cuda.synchronize()
+            out.append(a0.elapsed_time(a1) * 1e3)
+        return out[3:]
+
+    single = single_launches(lambda j: iqa.iqa_both(ctx, dx[j], dy[j], iqa.IQA_F32, N, NT,
+                                                    params, lisi[j], aug[j], None, stream), 63)
+    single_us = float(np.median(single))
+    lisi_only = single_launches(lambda j: iqa.iqa_lisi(ctx, dx[j], dy[j], iqa.IQA_F32, N, NT,
+                                                       params, lisi[j], None, stream), 13)
+    aug_only = single_launches(lambda j: iqa.iqa_auglisi(ctx, dx[j], dy[j], iqa.IQA_F32, N, NT,
+                                                         params, aug[j], None, stream), 13)
     plain_cfg = iqa.iqa_get_config(ctx, iqa.IQA_F32, N, NT, iqa.MAPS_BOTH).as_dict()
 
     # N_T sweep of the batched form (the paper's Fig. 1 axis)
@@ -640,9 +661,16 @@ def run_ours(args):
                 "GBs": round(pair_bytes / (per_pair_us * 1e-6) / 1e9, 1),
                 "us_per_pair": round(per_pair_us, 3),
                 "single_launch_us": round(single_us, 3),
+                "single_launch_us_median10": round(float(np.median(single[:10])), 3),
+                "single_launch_us_median60": round(single_us, 3),
+                "single_launch_us_min": round(float(np.min(single)), 3),
+                "lisi_only_single_us_median10": round(float(np.median(lisi_only)), 3),
+                "auglisi_only_single_us_median10": round(float(np.median(aug_only)), 3),
                 "launch": plain_cfg,
                 "timing": "back-to-back iqa_both launches replayed from a CUDA graph; "
-                          "single launch with a GPU-side delay queued ahead"},
+                          "single launches (60 of both maps, 10 of each map alone) each "
+                          "with a GPU-side delay queued ahead, rotating over the step's "
+                          "pairs so that no launch finds its pixels in L2"},
             "nt_sweep_GBs": sweep,
             "clocks": clk,
             "e2e": {"value": round(e2e_value, 2), "unit": "GB/s",

@@ -461,11 +461,13 @@ iqa_status iqa_server_add_reference(iqa_server *srv, int ref_id, const iqa_catal
  * `cat` on the device -- its sources minus drop[0..ndrop), plus a transient
  * with source add_src's profile at (add_x, add_y) and peak add_flux when
  * add_src >= 0, over noise from `seed` -- rounded to nearest into `dtype` at
- * `out` (device, N*N elements).  The catalogue is uploaded for the call and
+ * `out` (device, N*N elements, 16-byte aligned).  The catalogue is uploaded for the call and
  * freed after it; the call waits for the render to finish.  The recipe (a
- * counter-based Philox4x32-10 noise draw, sources in catalogue order) is
+ * counter-based Philox4x32-10 draw per four pixels, each word's byte sum an
+ * Irwin-Hall standard normal stand-in, sources added in catalogue order) is
  * reproducible on the host bit for bit.
- * Errors: IQA_ERR_INVALID_ARG (bad catalogue, drop list or transient),
+ * Errors: IQA_ERR_INVALID_ARG (bad catalogue, drop list or transient, or a
+ * misaligned `out`),
  * IQA_ERR_NOMEM, IQA_ERR_CUDA.
  */
 iqa_status iqa_render_epoch(iqa_ctx *ctx, const iqa_catalog *cat, unsigned long long seed,

@@ -229,6 +229,7 @@ TileArgs make_args(const void *x, const void *y, int N, int NT,
     a.C2f = (float)P.C2;
     a.Cf = (float)P.C;
     a.Df = (float)P.D;
+    a.Cd = P.C;
     a.lisi = lisi;
     a.aug = aug;
     a.sums = sums;

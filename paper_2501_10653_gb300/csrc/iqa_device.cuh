@@ -10,7 +10,8 @@
 // "unit": a rectangle of RH rows and TX whole tiles across (or, with a cluster
 // of S CTAs along y, 1/S of one tile's rows), with 16-byte non-caching loads,
 // the clamp and every term fused into that single read, per-thread FP32 sums
-// folded with Kahan compensation, and an FP32 shuffle-tree / cross-CTA combine.
+// folded with Kahan compensation, an FP32 shuffle-tree / cross-CTA combine,
+// and the per-tile ratios of Eq. 1 / Eq. 2 (FP64 where augLISI cancels).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -37,7 +38,8 @@ struct TileArgs {
     int LPT;            // vectors per tile row = NT / VEC
     int tile_row0;      // first tile row covered by this launch
     float C1f;          // C1 rounded to float, used in the per-pixel divide
-    float C2f, Cf, Df;  // Eq. 1 / Eq. 2 constants for the per-tile combine
+    float C2f, Cf, Df;  // Eq. 1 / Eq. 2 constants of the per-tile combine
+    double Cd;          // C, for the FP64 form of Eq. 2 (cancelling tiles)
     float *lisi;        // (T*T) map or nullptr
     float *aug;         // (T*T) map or nullptr
     double *sums;       // (T*T*4) or nullptr
@@ -148,29 +150,42 @@ __device__ __forceinline__ void unpack(const Raw<T, VEC> &r, float (&f)[VEC])
 }
 
 // ---------------------------------------------------------------------------
-// Approximate reciprocal: the PTX rcp.approx.f32 instruction (about one ulp
-// of error by the PTX ISA's bound; subnormals are not flushed).
+// Approximate reciprocal: the PTX rcp.approx.ftz.f32 instruction (about one
+// ulp of error by the PTX ISA's bound).  Its argument here is d + C1 >= C1, a
+// normal number, and its result is normal for every argument below 2^126, so
+// flushing subnormals changes nothing for pixel values in that range (any
+// radio image, whose pixels are Jy-scale).
 __device__ __forceinline__ float rcp_approx(float v)
 {
     float r;
-    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
     return r;
 }
 
+// Packed running sums of one thread: lane .x takes the even elements of each
+// vector, lane .y the odd ones (VEC == 1: lane .x only).
+struct Sums2 {
+    float2 a, b, x, y;
+    __device__ __forceinline__ void zero()
+    {
+        a = b = x = y = make_float2(0.0f, 0.0f);
+    }
+};
+
 // Per-pixel terms of Eq. 1 / Eq. 2 for the VEC pixel pairs of one 16-byte
-// vector of each image, summed in element order into (a, b, sx, sy):
-//   a = sum s / (d + C1),  b = sum s * d,  sx = sum x,  sy = sum y
-// with x, y clamped, s = x + y (= |x + y| after the clamp) and d = |x - y|.
-// Clamp: max(v, 0) returns 0 for v <= 0 and for NaN (the non-NaN operand);
-// 16-bit pixels are clamped two at a time in their packed form, then widened
-// to float exactly.  The divide s / (d + C1) is s * rcp(d + C1) (denominator
-// >= C1 > 0; about 2 ulp), fused into the accumulation, as is s * d.  The
-// even and odd elements of a vector are summed separately, two at a time with
-// the packed f32x2 operations (add.f32x2, fma.f32x2), then added.
+// vector of each image, added in element order to the running sums p:
+//   a += s / (d + C1),  b += s * d,  x += x',  y += y'
+// with x', y' clamped, s = x' + y' (= |x + y| after the clamp) and
+// d = |x' - y'|.  Clamp: max(v, 0) returns 0 for v <= 0 and for NaN (the
+// non-NaN operand); 16-bit pixels are clamped two at a time in their packed
+// form, then widened to float exactly.  The divide s / (d + C1) is
+// s * rcp(d + C1) (denominator >= C1 > 0; about 2 ulp), fused into the
+// accumulation, as is s * d.  Two pixel pairs per instruction with the packed
+// f32x2 operations (add.f32x2, fma.f32x2); the sums stay packed until the
+// caller folds them.
 template <typename T, int VEC, bool DO_A, bool DO_B>
 __device__ __forceinline__ void vector_terms(const Raw<T, VEC> &rx, const Raw<T, VEC> &ry,
-                                             float C1f, float &a, float &b, float &sx,
-                                             float &sy)
+                                             float C1f, Sums2 &p)
 {
     float xv[VEC], yv[VEC];
     if constexpr (VEC > 1 && !std::is_same<T, float>::value) {
@@ -212,16 +227,13 @@ __device__ __forceinline__ void vector_terms(const Raw<T, VEC> &rx, const Raw<T,
     if constexpr (VEC == 1) {
         const float s = xv[0] + yv[0];
         const float d = fabsf(xv[0] - yv[0]);
-        a = DO_A ? s * rcp_approx(d + C1f) : 0.0f;
-        b = DO_B ? s * d : 0.0f;
-        sx = xv[0];
-        sy = yv[0];
+        if (DO_A) p.a.x = __fmaf_rn(s, rcp_approx(d + C1f), p.a.x);
+        if (DO_B) p.b.x = __fmaf_rn(s, d, p.b.x);
+        p.x.x += xv[0];
+        p.y.x += yv[0];
     } else {
-        // two pixel pairs per instruction with the packed FP32 operations of
-        // this architecture; even and odd elements form two partial sums
         const float2 neg1 = make_float2(-1.0f, -1.0f);
         const float2 c1 = make_float2(C1f, C1f);
-        float2 a2 = make_float2(0.0f, 0.0f), b2 = a2, x2s = a2, y2s = a2;
 #pragma unroll
         for (int i = 0; i < VEC; i += 2) {
             const float2 x2 = make_float2(xv[i], xv[i + 1]);
@@ -232,16 +244,12 @@ __device__ __forceinline__ void vector_terms(const Raw<T, VEC> &rx, const Raw<T,
             if (DO_A) {
                 const float2 t2 = __fadd2_rn(d2, c1);
                 const float2 r2 = make_float2(rcp_approx(t2.x), rcp_approx(t2.y));
-                a2 = __ffma2_rn(s2, r2, a2);
+                p.a = __ffma2_rn(s2, r2, p.a);
             }
-            if (DO_B) b2 = __ffma2_rn(s2, d2, b2);
-            x2s = __fadd2_rn(x2s, x2);
-            y2s = __fadd2_rn(y2s, y2);
+            if (DO_B) p.b = __ffma2_rn(s2, d2, p.b);
+            p.x = __fadd2_rn(p.x, x2);
+            p.y = __fadd2_rn(p.y, y2);
         }
-        a = a2.x + a2.y;
-        b = b2.x + b2.y;
-        sx = x2s.x + x2s.y;
-        sy = y2s.x + y2s.y;
     }
 }
 
@@ -294,21 +302,17 @@ __device__ __forceinline__ void accumulate_unit(const T *__restrict__ xu,
                 row += 1;
             }
         }
-        float ba = 0.0f, bb = 0.0f, bx = 0.0f, by = 0.0f;
+        Sums2 p;
+        p.zero();
 #pragma unroll
         for (int u = 0; u < ILP; ++u) {
-            float a, b, sx, sy;
             // a vector that was not loaded is all zeros and adds exactly 0
-            vector_terms<T, VEC, DO_A, DO_B>(rx[u], ry[u], C1f, a, b, sx, sy);
-            ba += a;
-            bb += b;
-            bx += sx;
-            by += sy;
+            vector_terms<T, VEC, DO_A, DO_B>(rx[u], ry[u], C1f, p);
         }
-        if (DO_A) ka.add(ba);
-        if (DO_B) kb.add(bb);
-        kx.add(bx);
-        ky.add(by);
+        if (DO_A) ka.add(p.a.x + p.a.y);
+        if (DO_B) kb.add(p.b.x + p.b.y);
+        kx.add(p.x.x + p.x.y);
+        ky.add(p.y.x + p.y.y);
     }
     acc[0] = ka.value();
     acc[1] = kb.value();
@@ -428,15 +432,36 @@ __device__ __forceinline__ void reduce_unit(const float (&acc)[4], int TX, int L
     bar();
 }
 
-// Eq. 1 / Eq. 2 per-tile combine and the output writes.  IEEE float division
-// (correctly rounded): with nonnegative sums the ratios carry a few float
-// roundings, far inside the 1e-5 per-tile bound; the optional sums are
+// Eq. 1 / Eq. 2 per-tile combine and the output writes; the optional sums are
 // exported widened to FP64.
+//
+// Per-tile combine of Eq. 1 and Eq. 2 from the tile's four FP32 sums:
+//   lisi = D A / (max(Sx, Sy) + C2),   aug = 1 - B / (Sx + Sy + C).
+// lisi is a product and quotient of nonnegative values, so FP32 with IEEE
+// division (correctly rounded) keeps it within 3 u of the exact ratio of the
+// sums.  aug loses relative accuracy to cancellation when r = B/(Sx+Sy+C) is
+// close to 1: there (|aug| < r/16, rare on sky images, where aug is close to 1)
+// the ratio and the subtraction are redone in FP64 from the same sums and
+// rounded once, so aug keeps about 1 u relative on every tile.
+__device__ __forceinline__ void combine_tile(float *lisi, float *aug, long long t, float A,
+                                             float B, float Sx, float Sy, float C2f, float Cf,
+                                             float Df, double Cd)
+{
+    if (lisi) lisi[t] = __fdiv_rn(Df * A, fmaxf(Sx, Sy) + C2f);
+    if (aug) {
+        const float r = __fdiv_rn(B, (Sx + Sy) + Cf);
+        float v = 1.0f - r;
+        if (fabsf(v) < 0.0625f * r)
+            v = __double2float_rn(__dadd_rn(
+                1.0, -__ddiv_rn((double)B, __dadd_rn(__dadd_rn((double)Sx, (double)Sy), Cd))));
+        aug[t] = v;
+    }
+}
+
 __device__ __forceinline__ void write_tile(const TileArgs &p, long long t,
                                            float A, float B, float Sx, float Sy)
 {
-    if (p.lisi) p.lisi[t] = __fdiv_rn(p.Df * A, fmaxf(Sx, Sy) + p.C2f);
-    if (p.aug) p.aug[t] = 1.0f - __fdiv_rn(B, (Sx + Sy) + p.Cf);
+    combine_tile(p.lisi, p.aug, t, A, B, Sx, Sy, p.C2f, p.Cf, p.Df, p.Cd);
     if (p.sums) {
         double *o = p.sums + 4 * t;
         o[0] = A;

@@ -16,6 +16,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdint>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -551,8 +552,17 @@ void worker_main(iqa_server *srv)
             }
         }
         if (!launched) {
-            // nothing to launch: wait for new work, polling busy steps often
-            srv->cv_work.wait_for(lk, std::chrono::microseconds(any_busy ? 20 : 2000));
+            if (any_busy) {
+                // a step is on the GPU: poll its event again at once, with the
+                // lock released for submitters (a timed sleep here would add
+                // the kernel timer's slack, tens of microseconds, to every
+                // request's latency)
+                lk.unlock();
+                std::this_thread::yield();
+                lk.lock();
+            } else {
+                srv->cv_work.wait_for(lk, std::chrono::microseconds(2000));
+            }
         }
     }
 }
@@ -815,6 +825,10 @@ iqa_status iqa_render_epoch(iqa_ctx *ctx, const iqa_catalog *cat, unsigned long 
     if (!ctx || !out) return IQA_ERR_INVALID_ARG;
     if (!dtype_ok(dtype)) {
         set_error(ctx, "unknown dtype %d", (int)dtype);
+        return IQA_ERR_INVALID_ARG;
+    }
+    if (reinterpret_cast<uintptr_t>(out) % 16 != 0) {
+        set_error(ctx, "out must be 16-byte aligned");
         return IQA_ERR_INVALID_ARG;
     }
     iqa_status s = check_catalog(ctx, cat);

@@ -43,7 +43,9 @@ struct PairDesc {
     int LPU;                 // 16-byte vectors per unit row = TX * NT / VEC
     int LPT;                 // vectors per tile row = NT / VEC
     int pad_;
-    float C1f, C2f, Cf, Df;
+    float C1f;               // C1 rounded to float, used in the per-pixel divide
+    float C2f, Cf, Df;       // Eq. 1 / Eq. 2 constants of the per-tile combine
+    double Cd;               // C, for the FP64 form of Eq. 2 (cancelling tiles)
 };
 
 struct StreamParams {
@@ -171,8 +173,7 @@ __device__ __forceinline__ int find_pair(const PairDesc *d, int npairs, long lon
 __device__ __forceinline__ void write_tile_desc(const PairDesc &d, long long t, float A,
                                                 float B, float Sx, float Sy)
 {
-    if (d.lisi) d.lisi[t] = __fdiv_rn(d.Df * A, fmaxf(Sx, Sy) + d.C2f);
-    if (d.aug) d.aug[t] = 1.0f - __fdiv_rn(B, (Sx + Sy) + d.Cf);
+    combine_tile(d.lisi, d.aug, t, A, B, Sx, Sy, d.C2f, d.Cf, d.Df, d.Cd);
     if (d.sums) {
         double *o = d.sums + 4 * t;
         o[0] = A;
@@ -335,7 +336,8 @@ __global__ void __launch_bounds__(CT + 32, 1)
         }
         const uint4 *xs = reinterpret_cast<const uint4 *>(ring + (size_t)s * 2 * SB);
         const uint4 *ys = reinterpret_cast<const uint4 *>(ring + (size_t)s * 2 * SB + SB);
-        float ba = 0.0f, bb = 0.0f, bx = 0.0f, by = 0.0f;
+        Sums2 p;
+        p.zero();
         // four vectors of each image per thread per pass, loaded together
         for (int v0 = tid; v0 < V; v0 += 4 * CT) {
             Raw<T, VEC> rx[4], ry[4];
@@ -351,21 +353,14 @@ __global__ void __launch_bounds__(CT + 32, 1)
                 }
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float a, b, sx, sy;
-                vector_terms<T, VEC, DO_A, DO_B>(rx[j], ry[j], C1f, a, b, sx, sy);
-                ba += a;
-                bb += b;
-                bx += sx;
-                by += sy;
-            }
+            for (int j = 0; j < 4; ++j) vector_terms<T, VEC, DO_A, DO_B>(rx[j], ry[j], C1f, p);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
-        if (DO_A) ka.add(ba);
-        if (DO_B) kb.add(bb);
-        kx.add(bx);
-        ky.add(by);
+        if (DO_A) ka.add(p.a.x + p.a.y);
+        if (DO_B) kb.add(p.b.x + p.b.y);
+        kx.add(p.x.x + p.x.y);
+        ky.add(p.y.x + p.y.y);
         if (++c == chunks) {
             c = 0;
             const int TX = d->TX, LPU = d->LPU, LPT = d->LPT;

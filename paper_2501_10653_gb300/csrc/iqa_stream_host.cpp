@@ -163,6 +163,7 @@ iqa_status fill_pair_desc(iqa_ctx *ctx, PairDesc *d, const void *x, const void *
     d->C2f = (float)P.C2;
     d->Cf = (float)P.C;
     d->Df = (float)P.D;
+    d->Cd = P.C;
     return IQA_OK;
 }
 

@@ -8,13 +8,13 @@
 // (paper_2501_10653_gb300/synth.py, `render_epoch`) reproduces every pixel
 // bit for bit:
 //   * noise: the Philox4x32-10 counter-based generator (Salmon, Moraes, Dror
-//     and Shaw, SC'11) keyed by the seed, one call per pair of horizontally
+//     and Shaw, SC'11) keyed by the seed, one call per four horizontally
 //     adjacent pixels with counter (q low, q high, 0x5EED, 0), q = pixel
-//     index / 2; words 0-1 serve the even pixel and words 2-3 the odd one, each
-//     word giving two 16-bit uniforms (high half, low half) scaled by 2^-16;
-//     z = (u0+u1+u2+u3 - 2) * sqrt(3) (an Irwin-Hall sum of four, unit
-//     variance, bounded at +-sqrt(12)); every step is exact except the final
-//     multiply;
+//     index / 4; word k serves pixel 4q + k: its four bytes, summed as
+//     integers to s in [0, 1020], give z = (s - 510) * (sqrt(3) / 256) (an
+//     Irwin-Hall sum of four uniforms on the byte centres (b + 1/2) / 256:
+//     zero mean, variance 1 - 2^-16, bounded at +-sqrt(12)); the only
+//     rounding is the final multiply;
 //   * sources: each source i has an integer centre (x_i, y_i), a peak flux f_i
 //     and a 1-D float32 profile g_i[-h_i..h_i] computed on the host; its
 //     contribution to pixel (r, c) is (f_i * g_i[r - y_i]) * g_i[c - x_i],
@@ -50,36 +50,56 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
     return c;
 }
 
-// Irwin-Hall sum of four 16-bit uniforms: z = (u0+u1+u2+u3 - 2) * sqrt(3).
-__device__ __forceinline__ float irwin_hall4(uint32_t a, uint32_t b)
+// Irwin-Hall sum of the four bytes of one Philox word, standardised:
+// z = (b0 + b1 + b2 + b3 - 510) * sqrt(3) / 256.  The byte sum is formed with
+// two paired 16-bit adds; the integer is exact in float.
+constexpr float kNoiseScale = 1.7320508075688772f / 256.0f;  // exact: a power-of-2 step
+
+__device__ __forceinline__ float irwin_hall4_bytes(uint32_t w)
 {
-    const float scale = 1.0f / 65536.0f;
-    float s = __fmul_rn((float)(a >> 16), scale);
-    s = __fadd_rn(s, __fmul_rn((float)(a & 0xFFFFu), scale));
-    s = __fadd_rn(s, __fmul_rn((float)(b >> 16), scale));
-    s = __fadd_rn(s, __fmul_rn((float)(b & 0xFFFFu), scale));
-    return __fmul_rn(__fadd_rn(s, -2.0f), 1.7320508075688772f);
+    const uint32_t t = (w & 0x00FF00FFu) + ((w >> 8) & 0x00FF00FFu);
+    const int s = (int)((t & 0xFFFFu) + (t >> 16));
+    return __fmul_rn((float)(s - 510), kNoiseScale);
 }
 
-// Standardised noise of the two horizontally adjacent pixels 2q, 2q+1 (q =
-// pixel index / 2): one Philox call, words (0, 1) for the even pixel and
-// (2, 3) for the odd one.
-__device__ __forceinline__ float2 noise_pair(unsigned long long q, unsigned long long seed)
+// Standardised noise of the four horizontally adjacent pixels 4q .. 4q+3 (q
+// = pixel index / 4): one Philox call, word k for pixel 4q + k.
+__device__ __forceinline__ float4 noise_quad(unsigned long long q, unsigned long long seed)
 {
     const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), 0x5EEDu, 0u),
                                   make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-    return make_float2(irwin_hall4(w.x, w.y), irwin_hall4(w.z, w.w));
+    return make_float4(irwin_hall4_bytes(w.x), irwin_hall4_bytes(w.y), irwin_hall4_bytes(w.z),
+                       irwin_hall4_bytes(w.w));
 }
 
-template <typename T> __device__ __forceinline__ T to_storage(float v);
-template <> __device__ __forceinline__ float to_storage<float>(float v) { return v; }
-template <> __device__ __forceinline__ __half to_storage<__half>(float v)
+// Four consecutive pixels rounded to nearest into the storage type and
+// written with one vector store (16 bytes for FP32, 8 for 16-bit types; the
+// first pixel index is a multiple of 4 and the image 16-byte aligned).
+template <typename T> __device__ __forceinline__ void store4(T *out, const float (&v)[4]);
+template <> __device__ __forceinline__ void store4<float>(float *out, const float (&v)[4])
 {
-    return __float2half_rn(v);
+    *reinterpret_cast<float4 *>(out) = make_float4(v[0], v[1], v[2], v[3]);
 }
-template <> __device__ __forceinline__ __nv_bfloat16 to_storage<__nv_bfloat16>(float v)
+template <> __device__ __forceinline__ void store4<__half>(__half *out, const float (&v)[4])
 {
-    return __float2bfloat16_rn(v);
+    const __half2 a = __halves2half2(__float2half_rn(v[0]), __float2half_rn(v[1]));
+    const __half2 b = __halves2half2(__float2half_rn(v[2]), __float2half_rn(v[3]));
+    uint2 u;
+    u.x = *reinterpret_cast<const uint32_t *>(&a);
+    u.y = *reinterpret_cast<const uint32_t *>(&b);
+    *reinterpret_cast<uint2 *>(out) = u;
+}
+template <>
+__device__ __forceinline__ void store4<__nv_bfloat16>(__nv_bfloat16 *out, const float (&v)[4])
+{
+    const __nv_bfloat162 a =
+        __halves2bfloat162(__float2bfloat16_rn(v[0]), __float2bfloat16_rn(v[1]));
+    const __nv_bfloat162 b =
+        __halves2bfloat162(__float2bfloat16_rn(v[2]), __float2bfloat16_rn(v[3]));
+    uint2 u;
+    u.x = *reinterpret_cast<const uint32_t *>(&a);
+    u.y = *reinterpret_cast<const uint32_t *>(&b);
+    *reinterpret_cast<uint2 *>(out) = u;
 }
 
 __device__ __forceinline__ bool is_dropped(const SynthJob &j, int src)
@@ -90,37 +110,30 @@ __device__ __forceinline__ bool is_dropped(const SynthJob &j, int src)
 }
 
 // Work unit: one catalogue bin (kSynthBin x kSynthBin pixels) of one job per
-// block iteration; thread t takes the column pair 2 (t % 32), 2 (t % 32) + 1
-// of rows t / 32 + 8k, k < 8 (one Philox call per pair), so each warp writes
-// 64 consecutive pixels per step.  The jobs' first-bin offsets live in shared
-// memory (looked up once per bin), and so do the bin's sources (in catalogue
-// order, the order every pixel adds them in).
+// block iteration; thread t takes the four columns 4 (t % 16) .. 4 (t % 16) + 3
+// of rows t / 16 + 16k, k < 4 (one Philox call and one vector store per
+// four pixels), so each warp writes two 64-pixel row segments per step.  The
+// jobs' first-bin offsets live in shared memory (looked up once per bin), and
+// so do the bin's sources (in catalogue order, the order every pixel adds them
+// in).
 constexpr int kSynthThreads = 256;
 constexpr int kSynthMaxJobs = 64;
 constexpr int kSynthBinSrc = 64;  // bin sources staged in shared memory
+constexpr int kQuadsPerRow = kSynthBin / 4;
 
-__device__ __forceinline__ float sky_at(const SynthCatalog &cat, const SynthJob &j, int n,
-                                        const int *s_x, const int *s_y, const int *s_h,
-                                        const int *s_off, const float *s_f, int r, int c)
+// Adds one source's contribution (f * g[dy]) * g[dx] to the four pixels
+// (r, c .. c+3), for the pixels inside its window.
+__device__ __forceinline__ void add_source(float (&sky)[4], const float *g0, int h, int dy,
+                                           int dx0, float f)
 {
-    float sky = 0.0f;
-    for (int m = 0; m < n; ++m) {
-        const int h = s_h[m];
-        const int dy = r - s_y[m], dx = c - s_x[m];
-        if (dy < -h || dy > h || dx < -h || dx > h) continue;
-        const float *g = cat.profile + s_off[m] + h;
-        sky = __fadd_rn(sky, __fmul_rn(__fmul_rn(s_f[m], g[dy]), g[dx]));
+    if (dy < -h || dy > h || dx0 + 3 < -h || dx0 > h) return;
+    const float *g = g0 + h;
+    const float fy = __fmul_rn(f, g[dy]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int dx = dx0 + k;
+        if (dx >= -h && dx <= h) sky[k] = __fadd_rn(sky[k], __fmul_rn(fy, g[dx]));
     }
-    if (j.add_src >= 0) {
-        const int i = j.add_src;
-        const int h = cat.half[i];
-        const int dy = r - j.add_y, dx = c - j.add_x;
-        if (dy >= -h && dy <= h && dx >= -h && dx <= h) {
-            const float *g = cat.profile + cat.profile_off[i] + h;
-            sky = __fadd_rn(sky, __fmul_rn(__fmul_rn(j.add_flux, g[dy]), g[dx]));
-        }
-    }
-    return sky;
 }
 
 template <typename T>
@@ -135,9 +148,9 @@ __global__ void __launch_bounds__(kSynthThreads)
     const long long total_bins = header[1];
     for (int i = threadIdx.x; i < njobs; i += kSynthThreads) s_begin[i] = jobs[i].blocks_begin;
     __syncthreads();
-    const int lc = 2 * (threadIdx.x % (kSynthBin / 2));  // even column within the bin
-    const int lr0 = threadIdx.x / (kSynthBin / 2);       // first row within the bin
-    constexpr int kRowStep = kSynthThreads / (kSynthBin / 2);
+    const int lc = 4 * (threadIdx.x % kQuadsPerRow);  // first column within the bin
+    const int lr0 = threadIdx.x / kQuadsPerRow;       // first row within the bin
+    constexpr int kRowStep = kSynthThreads / kQuadsPerRow;
     for (long long b = blockIdx.x; b < total_bins; b += gridDim.x) {
         int lo = 0, hi = njobs - 1;
         while (lo < hi) {
@@ -175,13 +188,20 @@ __global__ void __launch_bounds__(kSynthThreads)
         for (int k = 0; k < kSynthBin / kRowStep; ++k) {
             const int r = br * kSynthBin + lr0 + k * kRowStep;
             const unsigned long long pix = (unsigned long long)r * j.N + c;
-            const float2 z = noise_pair(pix >> 1, j.seed);
-            const float v0 = __fadd_rn(sky_at(cat, j, n, s_x, s_y, s_h, s_off, s_f, r, c),
-                                       __fmul_rn(sigma, z.x));
-            const float v1 = __fadd_rn(sky_at(cat, j, n, s_x, s_y, s_h, s_off, s_f, r, c + 1),
-                                       __fmul_rn(sigma, z.y));
-            out[pix] = to_storage<T>(v0);
-            out[pix + 1] = to_storage<T>(v1);
+            const float4 z = noise_quad(pix >> 2, j.seed);
+            float sky[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            for (int m = 0; m < n; ++m)
+                add_source(sky, cat.profile + s_off[m], s_h[m], r - s_y[m], c - s_x[m], s_f[m]);
+            if (j.add_src >= 0) {
+                const int i = j.add_src;
+                add_source(sky, cat.profile + cat.profile_off[i], cat.half[i], r - j.add_y,
+                           c - j.add_x, j.add_flux);
+            }
+            const float v[4] = {__fadd_rn(sky[0], __fmul_rn(sigma, z.x)),
+                                __fadd_rn(sky[1], __fmul_rn(sigma, z.y)),
+                                __fadd_rn(sky[2], __fmul_rn(sigma, z.z)),
+                                __fadd_rn(sky[3], __fmul_rn(sigma, z.w))};
+            store4<T>(out + pix, v);
         }
         __syncthreads();  // s_* are reused by the next bin
     }

@@ -179,10 +179,11 @@ def precision_pair(i, N=8192, seed=3, dtype="f32"):
 # functions below make the same images on the host, bit for bit, so that tests
 # can feed the oracle inputs that never came from the CUDA path:
 #   * noise: Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11), key = seed,
-#     counter = (q low word, q high word, 0x5EED, 0) with q = pixel index / 2;
-#     words 0-1 give the even pixel's four 16-bit uniforms, words 2-3 the odd
-#     pixel's; their sum times 2^-16, minus 2, times sqrt(3) (Irwin-Hall of
-#     four: unit variance, bounded at +-sqrt(12));
+#     counter = (q low word, q high word, 0x5EED, 0) with q = pixel index / 4;
+#     word k serves pixel 4q + k: the sum s of its four bytes gives
+#     z = (s - 510) * (sqrt(3) / 256) in float32 (Irwin-Hall of four uniforms
+#     on the byte centres: zero mean, variance 1 - 2^-16, bounded at
+#     +-sqrt(12));
 #   * sources: integer centres, float32 1-D profiles g[-h..h]; contribution
 #     (f * g[dy]) * g[dx], added to the pixel in catalogue order;
 #   * pixel = sky + sigma * z in float32, rounded to nearest into storage.
@@ -212,24 +213,16 @@ def philox4x32_10(c0, c1, c2, c3, k0, k1):
 
 def epoch_noise(N, seed):
     """float32 N x N standardised noise z of the device generator: one Philox
-    call per pair of horizontally adjacent pixels (q = pixel index / 2), words
-    0-1 for the even pixel and 2-3 for the odd one, each word split into two
-    16-bit uniforms (high half first)."""
-    q = np.arange(N * N // 2, dtype=np.uint64)
+    call per four horizontally adjacent pixels (q = pixel index / 4), word k
+    for pixel 4q + k, z = (byte sum - 510) * (sqrt(3) / 256)."""
+    q = np.arange(N * N // 4, dtype=np.uint64)
     w = philox4x32_10(q & _MASK32, q >> np.uint64(32), np.uint64(0x5EED),
                       np.uint64(0), seed & 0xFFFFFFFF, seed >> 32)
-    scale = np.float32(1.0 / 65536.0)
-
-    def ih4(a, b):
-        s = (a >> np.uint64(16)).astype(np.float32) * scale
-        s = s + (a & np.uint64(0xFFFF)).astype(np.float32) * scale
-        s = s + (b >> np.uint64(16)).astype(np.float32) * scale
-        s = s + (b & np.uint64(0xFFFF)).astype(np.float32) * scale
-        return (s + np.float32(-2.0)) * np.float32(1.7320508075688772)
-
+    scale = np.float32(1.7320508075688772) / np.float32(256.0)
     z = np.empty(N * N, dtype=np.float32)
-    z[0::2] = ih4(w[0], w[1])
-    z[1::2] = ih4(w[2], w[3])
+    for k in range(4):
+        b = w[k].astype(np.uint32).view(np.uint8).reshape(-1, 4).astype(np.int32)
+        z[k::4] = (b.sum(axis=1) - 510).astype(np.float32) * scale
     return z.reshape(N, N)
 
 

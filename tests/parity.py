@@ -11,10 +11,13 @@ per-tile quantity within 1e-5 relative.
   the sums are perfectly conditioned; an oracle 0 must come back exactly 0.
 The bound follows from the arithmetic: each per-pixel term carries a few
 float32 roundings (<= ~4 u plus ~2 ulp for the approximate reciprocal,
-u = 2^-24); a thread sums a vector's <= 8 terms in order (<= 7 u), then <= 8
-vector partials in order (<= 7 u), Kahan-folded across batches (~2 u); the
-cross-thread shuffle trees and the cluster combine add <= ~16 float32
-additions.  The worst case is about 40 u = 2.4e-6, inside 1e-5.
+u = 2^-24); a thread keeps two packed running sums per quantity (even and odd
+elements) over one pass of at most 8 vectors, i.e. <= 32 terms each, added in
+order (<= 31 u), folds the pair (1 u) and Kahan-adds the pass into its total
+(~2 u); the cross-thread shuffle trees and the cluster combine add <= ~16
+float32 additions.  The worst case is about 55 u = 3.3e-6, inside 1e-5.  The
+per-tile ratios are IEEE float divisions of the sums (<= 3 u more); where
+augLISI cancels (|aug| < r/16) it is formed in FP64 and rounded once.
 """
 import numpy as np
 

@@ -415,3 +415,44 @@ def test_16bit_nan_and_negative_pixels_read_as_zero(ctx, orc, dt):
         v[rng.random(v.shape) < 0.02] = nan_bits
     want = parity.oracle_maps(orc, x, y, 64, PARAMS)
     parity.assert_parity(parity.gpu_maps(ctx, x, y, 64, PARAMS), want, PARAMS)
+
+
+def _cancelling_pair(dt):
+    """y = 0 and x constant a_t = 1 + k_t / 64 per 16x16 tile, k_t in -3..3:
+    r = B / (Sx + C) = a_t^2 m / (a_t m + C) is within 1/16 of 1, so
+    aug = 1 - r cancels (aug = C / (m + C), about 4e-9, at k_t = 0).  Every
+    term and every partial sum is a multiple of 2^-12 below 2^9, so the GPU's
+    FP32 sums are exact and aug's accuracy is the combine's alone."""
+    N, NT = 128, 16
+    T = N // NT
+    k = (np.arange(T * T) % 7 - 3).reshape(T, T)
+    a = (1.0 + k / 64.0).astype(np.float32)
+    x = np.kron(a, np.ones((NT, NT), np.float32)).astype(np.float32)
+    y = np.zeros_like(x)
+    return synth._cast(x.astype(np.float64), dt), synth._cast(y.astype(np.float64), dt), NT
+
+
+@pytest.mark.parametrize("dt", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_cancelling_aug_tiles_keep_relative_accuracy(ctx, orc, dt, variant):
+    """Where augLISI cancels (|aug| < r/16) the combine is redone in FP64: on
+    exactly summable tiles aug matches the oracle to 1e-6 relative, including
+    aug = C / (m + C) which an FP32 combine rounds to 0."""
+    from paper_2501_10653_gb300 import iqa
+    x, y, NT = _cancelling_pair(dt)
+    N = x.shape[0]
+    code = parity.dtype_code(x)
+    cfg = dict(variant=variant, threads=128, tiles_across=1)
+    if variant == 1:
+        cfg.update(stages=4, stage_kb=4)
+    iqa.iqa_set_config(ctx, code, N, NT, iqa.MAPS_BOTH, cfg)
+    try:
+        gl, ga, gs = parity.gpu_maps(ctx, x, y, NT, PARAMS)
+    finally:
+        iqa.iqa_set_config(ctx, code, N, NT, iqa.MAPS_BOTH, None)
+    ol, oa, osum = parity.oracle_maps(orc, x, y, NT, PARAMS)
+    assert np.array_equal(gs[:, 1:], osum[:, 1:])  # B, Sx, Sy exact
+    o = oa.ravel()
+    assert np.all(np.abs(o) < 0.05) and o.min() < 0 < o.max()
+    assert np.all(np.abs(ga.ravel() - o) <= 1e-6 * np.abs(o))
+    parity.assert_parity((gl, ga, gs), (ol, oa, osum), PARAMS)
