@@ -68,6 +68,7 @@ struct PairDesc;
 bool stream_config_valid(int N, int NT, iqa_dtype dtype, const TileConfig &c,
                          std::string *why);
 TileConfig default_stream_config(int N, int NT, iqa_dtype dtype);
+int unit_boxes(int N, int BW);
 int stream_tiles_across(int N, int NT, iqa_dtype dtype, int threads, long long unit_px);
 iqa_status fill_pair_desc(iqa_ctx *ctx, PairDesc *d, const void *x, const void *y, int N,
                           int NT, iqa_dtype dtype, const TileConfig &c, const iqa_params &P,

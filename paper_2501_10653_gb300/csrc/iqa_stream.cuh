@@ -18,6 +18,7 @@
 //     has in flight and returns, so the host sees a status instead of a hang.
 #pragma once
 
+#include <climits>
 #include <cuda.h>
 
 #include "iqa_device.cuh"
@@ -42,7 +43,9 @@ struct PairDesc {
     int chunks;              // chunks per unit = NT / CH
     int LPU;                 // 16-byte vectors per unit row = TX * NT / VEC
     int LPT;                 // vectors per tile row = NT / VEC
-    int pad_;
+    int NB;                  // 256-element boxes across a unit row: 1 = 2-D map
+                             // {N, N}, box {BW, CH}; > 1 = 3-D map
+                             // {256, N/256, N}, box {256, NB, CH}
     float C1f;               // C1 rounded to float, used in the per-pixel divide
     float C2f, Cf, Df;       // Eq. 1 / Eq. 2 constants of the per-tile combine
     double Cd;               // C, for the FP64 form of Eq. 2 (cancelling tiles)
@@ -127,6 +130,20 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
                  : "memory");
 }
 
+// 3-D tiled TMA load of one box at (0, seg, row): the image viewed as rows of
+// 256-element segments, so that a box of NB segments lands in shared memory
+// as NB * 256 contiguous elements per row.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int seg,
+                                            int row, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(seg), "r"(row),
+        "r"(smem_addr(bar))
+        : "memory");
+}
+
 // 2-D tiled TMA load of one box at (col, row) into shared memory.
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int col,
                                             int row, uint64_t *bar)
@@ -159,17 +176,6 @@ __device__ __forceinline__ void named_bar(int id, int count)
 }
 
 // Which pair owns global unit u (pairs are stored in unit order).
-__device__ __forceinline__ int find_pair(const PairDesc *d, int npairs, long long u)
-{
-    int lo = 0, hi = npairs - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (d[mid].unit_begin <= u) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 __device__ __forceinline__ void write_tile_desc(const PairDesc &d, long long t, float A,
                                                 float B, float Sx, float Sy)
 {
@@ -199,7 +205,8 @@ __global__ void __launch_bounds__(CT + 32, 1)
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)S * 2 * SB);
     uint64_t *empty = full + S;
     long long *stage_unit = reinterpret_cast<long long *>(empty + S);
-    float(*red)[CT] = reinterpret_cast<float(*)[CT]>(stage_unit + S);
+    int *stage_pair = reinterpret_cast<int *>(stage_unit + S);
+    float(*red)[CT] = reinterpret_cast<float(*)[CT]>(stage_unit + 2 * S);
     float *part = reinterpret_cast<float *>(red + 4);
     int *abort_flag = reinterpret_cast<int *>(part + kMaxTX * 4);
 
@@ -225,21 +232,37 @@ __global__ void __launch_bounds__(CT + 32, 1)
         long long k = 0;  // chunk counter of this CTA
         int last_pair = -1;
         bool ok = true;
-        long long u = blockIdx.x, u_next = -1, i = 0;
+        // Work is taken in grabs of consecutive units [u, u_end): one
+        // atomicAdd on the shared counter per grab, issued one grab ahead so
+        // that its latency hides behind the current grab's copies.  A grab
+        // spans about kGrabBytes of each image (several small units, or one).
+        constexpr uint32_t kGrabBytes = 65536;
+        long long u = blockIdx.x, u_end = u + 1, nxt = -1, nxt_end = -1, i = 0;
+        bool have_next = false;
         if (sp.inject_stall) ok = false;  // test hook: issue nothing at all
-        else if (sp.sched) u = (long long)atomicAdd(&sp.sched[0], 1ull);
+        else if (sp.sched) {
+            u = (long long)atomicAdd(&sp.sched[0], 1ull);
+            u_end = u + 1;
+        }
+        // pair of unit u: units are taken in increasing order, so the pair
+        // index only moves forward (a binary search only when u passes the
+        // next pair's first unit)
+        int pi = 0;
+        long long next_begin = npairs > 1 ? descs[1].unit_begin : LLONG_MAX;
         while (ok) {
-            // the next unit's index is fetched before this unit's copies are
-            // issued, so the atomic's latency hides behind them
-            if (u < total_units) {
-                if (sp.sched) u_next = (long long)atomicAdd(&sp.sched[0], 1ull);
-                else u_next = blockIdx.x + (++i) * (long long)gridDim.x;
-            }
             const bool last = u >= total_units;
-            const int pi = (!last && npairs > 1) ? find_pair(descs, npairs, u) : 0;
+            if (!last && u >= next_begin) {
+                int lo = pi + 1, hi = npairs - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (descs[mid].unit_begin <= u) lo = mid;
+                    else hi = mid - 1;
+                }
+                pi = lo;
+                next_begin = pi + 1 < npairs ? descs[pi + 1].unit_begin : LLONG_MAX;
+            }
             const PairDesc &d = descs[pi];
             const int nchunks = last ? 1 : d.chunks;
-            long long lu = 0;
             int col0 = 0, row0 = 0;
             uint32_t bytes = 0;
             if (!last) {
@@ -252,11 +275,24 @@ __global__ void __launch_bounds__(CT + 32, 1)
                     prefetch_tmap(&d.tmy);
                     last_pair = pi;
                 }
-                lu = u - d.unit_begin;
+                const long long lu = u - d.unit_begin;
                 const int trow = (int)(lu / d.units_x);
                 col0 = (int)(lu - (long long)trow * d.units_x) * d.TX * d.NT;
                 row0 = trow * d.NT;
                 bytes = (uint32_t)(d.CH * d.TX * d.NT * (int)sizeof(T));
+                if (!have_next) {
+                    if (sp.sched) {
+                        const uint32_t unit_bytes = bytes * (uint32_t)d.chunks;
+                        const unsigned g =
+                            unit_bytes >= kGrabBytes ? 1u : min(8u, kGrabBytes / unit_bytes);
+                        nxt = (long long)atomicAdd(&sp.sched[0], (unsigned long long)g);
+                        nxt_end = nxt + g;
+                    } else {
+                        nxt = blockIdx.x + (++i) * (long long)gridDim.x;
+                        nxt_end = nxt + 1;
+                    }
+                    have_next = true;
+                }
             }
             for (int c = 0; c < nchunks; ++c, ++k) {
                 const int s = (int)(k % S);
@@ -276,17 +312,30 @@ __global__ void __launch_bounds__(CT + 32, 1)
                     break;
                 }
                 stage_unit[s] = u;
+                stage_pair[s] = pi;
                 mbar_expect_tx(&full[s], 2 * bytes);
                 unsigned char *dst = ring + (size_t)s * 2 * SB;
-                tma_load_2d(dst, &d.tmx, col0, row0 + c * d.CH, &full[s]);
-                tma_load_2d(dst + SB, &d.tmy, col0, row0 + c * d.CH, &full[s]);
+                if (d.NB > 1) {
+                    tma_load_3d(dst, &d.tmx, col0 >> 8, row0 + c * d.CH, &full[s]);
+                    tma_load_3d(dst + SB, &d.tmy, col0 >> 8, row0 + c * d.CH, &full[s]);
+                } else {
+                    tma_load_2d(dst, &d.tmx, col0, row0 + c * d.CH, &full[s]);
+                    tma_load_2d(dst + SB, &d.tmy, col0, row0 + c * d.CH, &full[s]);
+                }
             }
             if (last) break;
-            u = u_next;
+            if (++u >= u_end) {
+                u = nxt;
+                u_end = nxt_end;
+                have_next = false;
+            }
         }
         if (sp.sched) {
             // every CTA has made its final fetch once the count reaches the
-            // grid size; the last one puts the counters back to zero
+            // grid size; the last one puts the counters back to zero (the
+            // fence orders this CTA's fetches, including a grab fetched ahead
+            // and never used, before its count)
+            __threadfence();
             if (atomicAdd(&sp.sched[1], 1ull) == (unsigned long long)gridDim.x - 1) {
                 atomicExch(&sp.sched[0], 0ull);
                 atomicExch(&sp.sched[1], 0ull);
@@ -324,7 +373,7 @@ __global__ void __launch_bounds__(CT + 32, 1)
             // a new unit: its descriptor fields are read once into registers
             u = stage_unit[s];
             if (u < 0) return;
-            d = &descs[npairs > 1 ? find_pair(descs, npairs, u) : 0];
+            d = &descs[stage_pair[s]];
             lu = u - d->unit_begin;
             V = d->CH * d->LPU;
             chunks = d->chunks;
@@ -338,8 +387,25 @@ __global__ void __launch_bounds__(CT + 32, 1)
         const uint4 *ys = reinterpret_cast<const uint4 *>(ring + (size_t)s * 2 * SB + SB);
         Sums2 p;
         p.zero();
-        // four vectors of each image per thread per pass, loaded together
-        for (int v0 = tid; v0 < V; v0 += 4 * CT) {
+        // Full passes of PASS vectors of each image per thread (eight for FP32,
+        // four for 16-bit types, whose vectors hold twice the pixels: the
+        // unrolled pass stays small enough for the instruction cache), all
+        // of a pass loaded before any is used; then a predicated tail of four
+        // (vectors past V read as zeros, which add exactly 0).
+        constexpr int PASS = VEC == 4 ? 8 : 4;
+        int v0 = tid;
+        for (; v0 + (PASS - 1) * CT < V; v0 += PASS * CT) {
+            Raw<T, VEC> rx[PASS], ry[PASS];
+#pragma unroll
+            for (int j = 0; j < PASS; ++j) {
+                rx[j].v = xs[v0 + j * CT];
+                ry[j].v = ys[v0 + j * CT];
+            }
+#pragma unroll
+            for (int j = 0; j < PASS; ++j)
+                vector_terms<T, VEC, DO_A, DO_B>(rx[j], ry[j], C1f, p);
+        }
+        for (; v0 < V; v0 += 4 * CT) {
             Raw<T, VEC> rx[4], ry[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -378,7 +444,7 @@ __global__ void __launch_bounds__(CT + 32, 1)
 
 inline size_t stream_smem_bytes(int stages, int stage_bytes, int ct)
 {
-    return (size_t)stages * 2 * stage_bytes + (size_t)2 * stages * 8 + (size_t)stages * 8 +
+    return (size_t)stages * 2 * stage_bytes + (size_t)2 * stages * 8 + (size_t)2 * stages * 8 +
            (size_t)4 * ct * 4 + (size_t)kMaxTX * 4 * 4 + 16;
 }
 

@@ -73,7 +73,9 @@ bool stream_config_valid(int N, int NT, iqa_dtype dtype, const TileConfig &c,
     const int T = N / NT;
     if (c.TX < 1 || c.TX > kMaxTX || T % c.TX) return fail("tiles_across must divide N/NT");
     const int BW = c.TX * NT;
-    if (BW > 256) return fail("tiles_across * NT must be <= 256 for the TMA kernel");
+    if (!unit_boxes(N, BW))
+        return fail("tiles_across * NT must be <= 256, or a multiple of 256 up to 1024 "
+                    "with N a multiple of 256, for the TMA kernel");
     const int LPU = BW / V;
     if (c.TX > 1 && c.threads % LPU) return fail("threads must be a multiple of the unit row");
     if (!chunk_rows(NT, BW, es, c.stage_kb * 1024))
@@ -84,17 +86,28 @@ bool stream_config_valid(int N, int NT, iqa_dtype dtype, const TileConfig &c,
     return true;
 }
 
-// Widest unit (whole tiles, <= 256 elements across, <= unit_px pixel pairs)
-// whose row of 16-byte vectors divides the consumer thread count.
+// A unit row of `BW` elements is copied as one 2-D box (BW <= 256) or as a
+// 3-D box of BW / 256 segments of 256 elements (BW a multiple of 256, at most
+// 1024, and N a multiple of 256); 0 if neither fits.
+int unit_boxes(int N, int BW)
+{
+    if (BW <= 256) return 1;
+    if (BW % 256 || N % 256 || BW > 1024) return 0;
+    return BW / 256;
+}
+
+// Widest unit (whole tiles, <= unit_px pixel pairs, copied as unit_boxes()
+// boxes) whose row of 16-byte vectors divides the consumer thread count.
 int stream_tiles_across(int N, int NT, iqa_dtype dtype, int threads, long long unit_px)
 {
     const int V = 16 / elem_size(dtype);
     const int T = N / NT;
     int best = 1;
-    for (int tx = 2; tx <= kMaxTX && tx * NT <= 256; ++tx) {
+    for (int tx = 2; tx <= kMaxTX && tx * NT <= 1024; ++tx) {
         if (T % tx) continue;
         if ((long long)tx * NT * NT > unit_px) break;
         if (threads % (tx * NT / V)) continue;
+        if (!unit_boxes(N, tx * NT)) continue;
         best = tx;
     }
     return best;
@@ -129,14 +142,34 @@ iqa_status fill_pair_desc(iqa_ctx *ctx, PairDesc *d, const void *x, const void *
     CUtensorMapDataType dt = dtype == IQA_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                              : dtype == IQA_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)N};
-    cuuint64_t strides[1] = {(cuuint64_t)N * es};
-    cuuint32_t box[2] = {(cuuint32_t)BW, (cuuint32_t)CH};
-    cuuint32_t estr[2] = {1, 1};
+    const int NB = unit_boxes(N, BW);
+    // NB == 1: the image as a 2-D array {N, N}, box {BW, CH}.  NB > 1: the
+    // image as {256, N / 256, N} (a row of 256-element segments), box
+    // {256, NB, CH}, which lands as CH rows of BW contiguous elements.
+    const cuuint32_t rank = NB > 1 ? 3 : 2;
+    cuuint64_t dims[3], strides[2];
+    cuuint32_t box[3];
+    if (NB > 1) {
+        dims[0] = 256;
+        dims[1] = (cuuint64_t)N / 256;
+        dims[2] = (cuuint64_t)N;
+        strides[0] = (cuuint64_t)256 * es;
+        strides[1] = (cuuint64_t)N * es;
+        box[0] = 256;
+        box[1] = (cuuint32_t)NB;
+        box[2] = (cuuint32_t)CH;
+    } else {
+        dims[0] = (cuuint64_t)N;
+        dims[1] = (cuuint64_t)N;
+        strides[0] = (cuuint64_t)N * es;
+        box[0] = (cuuint32_t)BW;
+        box[1] = (cuuint32_t)CH;
+    }
+    cuuint32_t estr[3] = {1, 1, 1};
     const void *bases[2] = {x, y};
     CUtensorMap *maps[2] = {&d->tmx, &d->tmy};
     for (int i = 0; i < 2; ++i) {
-        CUresult r = enc(maps[i], dt, 2, const_cast<void *>(bases[i]), dims, strides, box,
+        CUresult r = enc(maps[i], dt, rank, const_cast<void *>(bases[i]), dims, strides, box,
                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -159,6 +192,7 @@ iqa_status fill_pair_desc(iqa_ctx *ctx, PairDesc *d, const void *x, const void *
     d->chunks = NT / CH;
     d->LPU = BW / V;
     d->LPT = NT / V;
+    d->NB = NB;
     d->C1f = (float)P.C1;
     d->C2f = (float)P.C2;
     d->Cf = (float)P.C;

@@ -268,7 +268,8 @@ def _stream_configs(N, NT, es):
     V = 16 // es
     T = N // NT
     for threads in (128, 256, 512):
-        for TX in [d for d in range(1, 65) if T % d == 0 and d * NT <= 256]:
+        for TX in [d for d in range(1, 65) if T % d == 0 and (d * NT <= 256 or (
+                d * NT <= 1024 and d * NT % 256 == 0 and N % 256 == 0))]:
             for stage_kb in (2, 4, 8, 16):
                 for stages, cps in ((4, 1), (8, 1), (3, 2)):
                     yield dict(variant=1, threads=threads, tiles_across=TX,
@@ -279,7 +280,8 @@ def _stream_configs(N, NT, es):
 @pytest.mark.parametrize("N,NT", [(512, 16), (512, 64), (512, 256), (480, 48), (384, 128)])
 def test_tma_persistent_kernel_every_shape(ctx, orc, dt, N, NT):
     """The persistent TMA-pipelined kernel (variant 1) against the oracle over
-    every valid launch shape: consumer counts, units of several tiles, stage
+    every valid launch shape: consumer counts, units of several tiles (up to
+    1024 elements wide, copied as 3-D boxes of 256-element segments), stage
     sizes that split a tile into 1..64 chunks, ring depths, 1 or 2 CTAs/SM."""
     from paper_2501_10653_gb300 import iqa
     es = 4 if dt == "f32" else 2
