@@ -112,6 +112,7 @@ enum ReqState { REQ_PENDING, REQ_INFLIGHT, REQ_DONE, REQ_FAILED };
 struct Request {
     iqa_handle h = 0;
     iqa_request r{};
+    Reference ref;  // copied at submission (references are never removed)
     int N = 0, T = 0;
     size_t epoch_bytes = 0, pool_off = 0;
     ReqState state = REQ_PENDING;
@@ -130,6 +131,11 @@ struct Slot {
     Clock::time_point t_launch;
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
+    // the step's work tables, one block in page-locked memory and its device
+    // copy (one upload per step): generator header {njobs, total_bins}, map
+    // kernel header {npairs, total_units}, generator jobs, pair descriptors
+    unsigned char *h_tab = nullptr, *d_tab = nullptr;
+    size_t tab_bytes = 0;
     SynthJob *d_jobs = nullptr, *h_jobs = nullptr;
     long long *d_synth_hdr = nullptr, *h_synth_hdr = nullptr;
     PairDesc *d_pairs = nullptr, *h_pairs = nullptr;
@@ -159,7 +165,8 @@ struct iqa_server {
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    bool stop = false;
+    std::atomic<bool> stop{false};
+    std::atomic<unsigned long long> n_submitted{0};  // read by the worker without mu
     std::thread worker;
 
     std::unordered_map<int, Reference> refs;
@@ -189,17 +196,11 @@ void free_slot(Slot &s)
         if (s.exec[g]) cudaGraphExecDestroy(s.exec[g]);
         if (s.graph[g]) cudaGraphDestroy(s.graph[g]);
     }
-    cudaFree(s.d_jobs);
-    cudaFree(s.d_synth_hdr);
-    cudaFree(s.d_pairs);
-    cudaFree(s.d_dyn);
+    cudaFree(s.d_tab);
     cudaFree(s.d_sched);
     cudaFree(s.d_status);
     cudaFree(s.d_out);
-    cudaFreeHost(s.h_jobs);
-    cudaFreeHost(s.h_synth_hdr);
-    cudaFreeHost(s.h_pairs);
-    cudaFreeHost(s.h_dyn);
+    cudaFreeHost(s.h_tab);
     cudaFreeHost(s.h_status);
     cudaFreeHost(s.h_out);
     if (s.ev) cudaEventDestroy(s.ev);
@@ -236,16 +237,8 @@ cudaError_t capture_slot(iqa_server *srv, Slot &s)
         s.grid[g] = grid;
         cudaError_t e = cudaStreamBeginCapture(s.st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return e;
-        cudaError_t e1 = cudaMemcpyAsync(s.d_jobs, s.h_jobs, sizeof(SynthJob) * M,
-                                         cudaMemcpyHostToDevice, s.st);
-        if (e1 == cudaSuccess)
-            e1 = cudaMemcpyAsync(s.d_synth_hdr, s.h_synth_hdr, 16, cudaMemcpyHostToDevice,
-                                 s.st);
-        if (e1 == cudaSuccess)
-            e1 = cudaMemcpyAsync(s.d_pairs, s.h_pairs, sizeof(PairDesc) * M,
-                                 cudaMemcpyHostToDevice, s.st);
-        if (e1 == cudaSuccess)
-            e1 = cudaMemcpyAsync(s.d_dyn, s.h_dyn, 16, cudaMemcpyHostToDevice, s.st);
+        cudaError_t e1 =
+            cudaMemcpyAsync(s.d_tab, s.h_tab, s.tab_bytes, cudaMemcpyHostToDevice, s.st);
         if (e1 == cudaSuccess)
             e1 = launch_synth((int)srv->cfg.dtype, s.d_jobs, s.d_synth_hdr, sgrid, s.st);
         if (e1 == cudaSuccess) {
@@ -266,27 +259,29 @@ cudaError_t alloc_slot(iqa_server *srv, Slot &s)
     const int M = srv->cfg.max_pairs_per_step;
     cudaError_t e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc(&s.d_jobs, sizeof(SynthJob) * M);
-    if (e == cudaSuccess) e = cudaMalloc(&s.d_synth_hdr, 16);
-    if (e == cudaSuccess) e = cudaMalloc(&s.d_pairs, sizeof(PairDesc) * M);
-    if (e == cudaSuccess) e = cudaMalloc(&s.d_dyn, 16);
+    // table block: headers at 0 and 16, jobs at 64, descriptors 64-aligned
+    const size_t off_jobs = 64;
+    const size_t off_pairs = round_up(off_jobs + sizeof(SynthJob) * M, 64);
+    s.tab_bytes = off_pairs + sizeof(PairDesc) * M;
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_tab, s.tab_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&s.d_sched, 256);
     if (e == cudaSuccess) e = cudaMemset(s.d_sched, 0, 256);
     if (e == cudaSuccess) e = cudaMalloc(&s.d_status, 256);
     if (e == cudaSuccess) e = cudaMemset(s.d_status, 0, 256);
-    if (e == cudaSuccess) e = cudaMallocHost(&s.h_jobs, sizeof(SynthJob) * M);
-    if (e == cudaSuccess) e = cudaMallocHost(&s.h_synth_hdr, 16);
-    if (e == cudaSuccess) e = cudaMallocHost(&s.h_pairs, sizeof(PairDesc) * M);
-    if (e == cudaSuccess) e = cudaMallocHost(&s.h_dyn, 16);
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_tab, s.tab_bytes);
     if (e == cudaSuccess) e = cudaMallocHost(&s.h_status, 256);
     if (e == cudaSuccess) {
-        std::memset(s.h_jobs, 0, sizeof(SynthJob) * M);
-        std::memset(s.h_pairs, 0, sizeof(PairDesc) * M);
-        std::memset(s.h_synth_hdr, 0, 16);
-        std::memset(s.h_dyn, 0, 16);
+        std::memset(s.h_tab, 0, s.tab_bytes);
+        e = cudaMemset(s.d_tab, 0, s.tab_bytes);
+        s.h_synth_hdr = reinterpret_cast<long long *>(s.h_tab);
+        s.h_dyn = s.h_synth_hdr + 2;
+        s.h_jobs = reinterpret_cast<SynthJob *>(s.h_tab + off_jobs);
+        s.h_pairs = reinterpret_cast<PairDesc *>(s.h_tab + off_pairs);
+        s.d_synth_hdr = reinterpret_cast<long long *>(s.d_tab);
+        s.d_dyn = s.d_synth_hdr + 2;
+        s.d_jobs = reinterpret_cast<SynthJob *>(s.d_tab + off_jobs);
+        s.d_pairs = reinterpret_cast<PairDesc *>(s.d_tab + off_pairs);
     }
-    if (e == cudaSuccess) e = cudaMemset(s.d_dyn, 0, 16);
-    if (e == cudaSuccess) e = cudaMemset(s.d_synth_hdr, 0, 16);
     if (e == cudaSuccess && !srv->cfg.one_pair_per_launch) {
         // one launch of each kernel with empty work before capture, so that
         // launch attributes are set outside the capture
@@ -343,7 +338,7 @@ iqa_status launch_step(iqa_server *srv, Slot &s)
     const int n = (int)s.reqs.size();
     for (int k = 0; k < n; ++k) {
         Request &r = *s.reqs[k];
-        const Reference &ref = srv->refs.at(r.r.ref_id);
+        const Reference &ref = r.ref;
         void *epoch = pool + r.pool_off;
         SynthJob &j = s.h_jobs[k];
         std::memset(&j, 0, sizeof j);
@@ -377,10 +372,11 @@ iqa_status launch_step(iqa_server *srv, Slot &s)
     if (srv->cfg.one_pair_per_launch) {
         // baseline: the plain path, one pair, no graph
         Request &r = *s.reqs[0];
-        const Reference &ref = srv->refs.at(r.r.ref_id);
-        e = cudaMemcpyAsync(s.d_jobs, s.h_jobs, sizeof(SynthJob), cudaMemcpyHostToDevice, s.st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(s.d_synth_hdr, s.h_synth_hdr, 16, cudaMemcpyHostToDevice, s.st);
+        const Reference &ref = r.ref;
+        // headers and the one job: the start of the table block
+        e = cudaMemcpyAsync(s.d_tab, s.h_tab,
+                            reinterpret_cast<unsigned char *>(s.h_jobs + 1) - s.h_tab,
+                            cudaMemcpyHostToDevice, s.st);
         if (e == cudaSuccess)
             e = launch_synth((int)srv->cfg.dtype, s.d_jobs, s.d_synth_hdr, srv->synth_grid, s.st);
         if (e == cudaSuccess) {
@@ -418,7 +414,8 @@ bool step_finished(iqa_server *srv, Slot &s, iqa_status *st)
 {
     *st = IQA_OK;
     if (srv->cfg.simulate) {
-        if (srv->cfg.simulate == 2) return false;  // a completion source that stalls
+        // a completion source that stalls (until the server is destroyed)
+        if (srv->cfg.simulate == 2) return srv->stop.load();
         const double need_ms = 1e3 * (double)s.bytes / std::max(1.0, srv->cfg.sim_bytes_per_s);
         return ms_between(s.t_launch, Clock::now()) >= need_ms;
     }
@@ -493,10 +490,46 @@ void retire(iqa_server *srv, Slot &s)
     srv->cv_done.notify_all();
 }
 
+// The worker keeps polling for this long after its last step before it
+// blocks on the condition variable (one host core while requests flow).
+constexpr double kIdleSpinMs = 5.0;
+// Longest stretch of polling without the lock before the worker takes it to
+// run its watchdog and admission checks.
+constexpr double kPollSliceMs = 0.1;
+
+// True when a busy slot's step looks finished.  Worker thread only: slots are
+// written by the worker alone, so this needs no lock.
+bool any_step_ready(iqa_server *srv)
+{
+    for (auto &s : srv->slots) {
+        if (!s.busy) continue;
+        iqa_status st;
+        if (step_finished(srv, s, &st)) return true;
+    }
+    return false;
+}
+
+// Polls, without holding srv->mu, until a step finishes, a request arrives,
+// the server stops, or kPollSliceMs pass.
+void poll_unlocked(iqa_server *srv, unsigned long long seen)
+{
+    const auto t0 = Clock::now();
+    while (!any_step_ready(srv)) {
+        if (srv->n_submitted.load(std::memory_order_acquire) != seen) return;
+        if (srv->stop.load()) return;
+        if (ms_between(t0, Clock::now()) > kPollSliceMs) return;
+        std::this_thread::yield();
+    }
+}
+
+// The worker holds srv->mu only for bookkeeping (retiring steps, admission,
+// statistics); GPU calls and polling run without it, so that submitters and
+// pollers never wait behind a launch.
 void worker_main(iqa_server *srv)
 {
     if (!srv->cfg.simulate) cudaSetDevice(srv->device);
     std::unique_lock<std::mutex> lk(srv->mu);
+    Clock::time_point t_active = Clock::now();
     while (true) {
         bool any_busy = false;
         for (auto &s : srv->slots) {
@@ -532,9 +565,12 @@ void worker_main(iqa_server *srv)
             }
             if (!s.reqs.empty()) {
                 s.busy = true;
-                iqa_status st = launch_step(srv, s);
                 ++srv->steps;
                 srv->step_pairs += (long long)s.reqs.size();
+                // the slot's requests are the worker's alone until retired
+                lk.unlock();
+                const iqa_status st = launch_step(srv, s);
+                lk.lock();
                 if (st != IQA_OK) {
                     // nothing was enqueued that will complete: fail and release now
                     const auto now = Clock::now();
@@ -551,14 +587,18 @@ void worker_main(iqa_server *srv)
                 launched = true;
             }
         }
+        if (launched || any_busy) t_active = Clock::now();
         if (!launched) {
-            if (any_busy) {
-                // a step is on the GPU: poll its event again at once, with the
-                // lock released for submitters (a timed sleep here would add
-                // the kernel timer's slack, tens of microseconds, to every
+            if (any_busy || ms_between(t_active, Clock::now()) < kIdleSpinMs) {
+                // a step is on the GPU, or one ended moments ago: poll at
+                // once, without the lock (a timed sleep, or a wake-up through
+                // the condition variable, would add the kernel's timer slack
+                // or scheduling delay, tens of microseconds, to the next
                 // request's latency)
+                const unsigned long long seen =
+                    srv->n_submitted.load(std::memory_order_acquire);
                 lk.unlock();
-                std::this_thread::yield();
+                poll_unlocked(srv, seen);
                 lk.lock();
             } else {
                 srv->cv_work.wait_for(lk, std::chrono::microseconds(2000));
@@ -901,6 +941,7 @@ static iqa_status submit_impl(iqa_server *srv, const iqa_request *req, iqa_handl
             return IQA_ERR_INVALID_ARG;
         }
     }
+    r->ref = it->second;
     r->N = N;
     r->T = N / req->NT;
     r->epoch_bytes = (size_t)N * N * srv->es;
@@ -922,6 +963,7 @@ static iqa_status submit_impl(iqa_server *srv, const iqa_request *req, iqa_handl
     srv->pending.push_back(r);
     srv->all[r->h] = r;
     *out = r->h;
+    srv->n_submitted.fetch_add(1, std::memory_order_release);
     srv->cv_work.notify_one();
     return IQA_OK;
 }
@@ -1054,10 +1096,7 @@ void iqa_server_destroy(iqa_server *srv)
     if (!srv) return;
     {
         std::lock_guard<std::mutex> g(srv->mu);
-        srv->stop = true;
-        // a stalled simulated step would never end: let the worker leave
-        if (srv->cfg.simulate == 2)
-            for (auto &s : srv->slots) s.busy = false;
+        srv->stop = true;  // a stalled simulated step ends when stop is set
     }
     srv->cv_work.notify_all();
     if (srv->worker.joinable()) srv->worker.join();
