@@ -54,8 +54,8 @@ PROFILED_TRAFFIC = {
                 "paper_2501_10653_gb300/csrc/iqa_stream.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream_launch.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream_f32.cu"],
-    "sha256": "ef33f77a7e2098c1b1f81c9ae8e1f49c3a50b2c99c9369a9705231fa3ac96716",
-    "bytes_per_pair": (268488448 + 3964160) / 8,
+    "sha256": "8c30136b67afc3a07f89b299d30c97cf620506a52de4872ce6d8994ca214dd3d",
+    "bytes_per_pair": (268492800 + 3802368) / 8,
     "capture": "8 pairs per launch, scaled by pairs to the timed launch",
 }
 PAPER_H100 = {"lisi_kernel_ms": 0.101, "auglisi_kernel_ms": 0.091,
