@@ -664,13 +664,16 @@ def run_ours(args):
                 "single_launch_us_median10": round(float(np.median(single[:10])), 3),
                 "single_launch_us_median60": round(single_us, 3),
                 "single_launch_us_min": round(float(np.min(single)), 3),
+                "single_launch_us_mean": round(float(np.mean(single)), 3),
                 "lisi_only_single_us_median10": round(float(np.median(lisi_only)), 3),
                 "auglisi_only_single_us_median10": round(float(np.median(aug_only)), 3),
                 "launch": plain_cfg,
                 "timing": "back-to-back iqa_both launches replayed from a CUDA graph; "
                           "single launches (60 of both maps, 10 of each map alone) each "
                           "with a GPU-side delay queued ahead, rotating over the step's "
-                          "pairs so that no launch finds its pixels in L2"},
+                          "pairs so that no launch finds its pixels in L2; isolated event "
+                          "times are quantised to about 2 us on this GPU, so the mean of 60 "
+                          "is the finer figure"},
             "nt_sweep_GBs": sweep,
             "clocks": clk,
             "e2e": {"value": round(e2e_value, 2), "unit": "GB/s",
