@@ -248,23 +248,39 @@ def serving_catalog(N, ref_index, seed=4, fwhm=4.0, flux=(0.005, 2.0), noise=2e-
     }
 
 
-def render_epoch(cat, seed, drop=(), add=None, dtype="f32"):
-    """Host mirror of the device epoch generator.  add = (src, x, y, flux) puts
-    a transient with source `src`'s profile at (x, y)."""
+def _noise_window(N, seed, r0, r1, c0, c1):
+    """epoch_noise(N, seed)[r0:r1, c0:c1], computed for those pixels only
+    (pixel p = r N + c takes word p % 4 of the Philox call for p / 4)."""
+    rows = np.arange(r0, r1, dtype=np.uint64)[:, None]
+    cols = np.arange(c0, c1, dtype=np.uint64)[None, :]
+    p = rows * np.uint64(N) + cols
+    q = p >> np.uint64(2)
+    w = philox4x32_10(q & _MASK32, q >> np.uint64(32), np.uint64(0x5EED), np.uint64(0),
+                      seed & 0xFFFFFFFF, seed >> 32)
+    word = np.choose((p & np.uint64(3)).astype(np.int64), w)
+    b = sum((word >> np.uint64(8 * k)) & np.uint64(0xFF) for k in range(4)).astype(np.int64)
+    scale = np.float32(1.7320508075688772) / np.float32(256.0)
+    return (b - 510).astype(np.float32) * scale
+
+
+def render_epoch_window(cat, seed, r0, r1, c0, c1, drop=(), add=None, dtype="f32"):
+    """render_epoch(cat, seed, drop, add, dtype)[r0:r1, c0:c1], computed for
+    that window only (the same float32 operations, pixel by pixel)."""
     N = cat["N"]
-    sky = np.zeros((N, N), dtype=np.float32)
+    sky = np.zeros((r1 - r0, c1 - c0), dtype=np.float32)
     drop = set(int(d) for d in drop)
 
     def put(i, cx, cy, f):
         h = int(cat["half"][i])
         g = cat["profile"][cat["profile_off"][i]:cat["profile_off"][i] + 2 * h + 1]
-        r0, r1 = max(0, cy - h), min(N, cy + h + 1)
-        c0, c1 = max(0, cx - h), min(N, cx + h + 1)
-        if r0 >= r1 or c0 >= c1:
+        a0, a1 = max(r0, cy - h), min(r1, cy + h + 1)
+        b0, b1 = max(c0, cx - h), min(c1, cx + h + 1)
+        if a0 >= a1 or b0 >= b1:
             return
-        gy = np.float32(f) * g[r0 - cy + h:r1 - cy + h]
-        gx = g[c0 - cx + h:c1 - cx + h]
-        sky[r0:r1, c0:c1] = sky[r0:r1, c0:c1] + gy[:, None] * gx[None, :]
+        gy = np.float32(f) * g[a0 - cy + h:a1 - cy + h]
+        gx = g[b0 - cx + h:b1 - cx + h]
+        sky[a0 - r0:a1 - r0, b0 - c0:b1 - c0] = (sky[a0 - r0:a1 - r0, b0 - c0:b1 - c0]
+                                                 + gy[:, None] * gx[None, :])
 
     for i in range(len(cat["x"])):
         if i in drop:
@@ -272,8 +288,19 @@ def render_epoch(cat, seed, drop=(), add=None, dtype="f32"):
         put(i, int(cat["x"][i]), int(cat["y"][i]), cat["flux"][i])
     if add is not None:
         put(int(add[0]), int(add[1]), int(add[2]), np.float32(add[3]))
-    img = sky + np.float32(cat["noise_sigma"]) * epoch_noise(N, seed)
+    if (r0, r1, c0, c1) == (0, N, 0, N):
+        z = epoch_noise(N, seed)
+    else:
+        z = _noise_window(N, seed, r0, r1, c0, c1)
+    img = sky + np.float32(cat["noise_sigma"]) * z
     return _cast(img.astype(np.float32), dtype) if dtype != "f32" else img
+
+
+def render_epoch(cat, seed, drop=(), add=None, dtype="f32"):
+    """Host mirror of the device epoch generator.  add = (src, x, y, flux) puts
+    a transient with source `src`'s profile at (x, y)."""
+    N = cat["N"]
+    return render_epoch_window(cat, seed, 0, N, 0, N, drop, add, dtype)
 
 
 def catalog_without_faintest(cat, k):

@@ -131,3 +131,25 @@ def assert_parity(got, want, params=None, rel=REL):
         assert_sums_close(gs, osums, rel)
         gr = gs[:, 1] / (gs[:, 2] + gs[:, 3] + p["C"])
         assert_lisi_close(gr, r, rel, "r = 1 - aug")
+
+
+def oracle_tile(orc, xw, yw, params=None):
+    """The oracle on one N_T x N_T tile given as its two pixel windows:
+    (lisi, aug, sums[4], r)."""
+    p = params or {"C1": 1e-6, "C2": 1e-6, "C": 1e-6, "D": 0.0}
+    NT = xw.shape[0]
+    ol, oa, os_ = oracle_maps(orc, np.ascontiguousarray(xw), np.ascontiguousarray(yw), NT, p)
+    s = os_[0]
+    return float(ol.ravel()[0]), float(oa.ravel()[0]), s, s[1] / (s[2] + s[3] + p["C"])
+
+
+def assert_sampled(got_lisi, got_aug, picks, want, params=None, rel=REL):
+    """got_*: full GPU maps (flat); picks: tile indices; want: oracle_tile()
+    results for those tiles, in the same order."""
+    gl = np.asarray(got_lisi).ravel()[picks]
+    ga = np.asarray(got_aug).ravel()[picks]
+    ol = np.array([w[0] for w in want])
+    oa = np.array([w[1] for w in want])
+    r = np.array([w[3] for w in want])
+    assert_lisi_close(gl, ol, rel)
+    assert_aug_close(ga, oa, r, rel)

@@ -1,0 +1,196 @@
+"""Parity at the workloads' full sizes, in the launch configurations that
+bench.py times (needs a GPU):
+
+* 32 distinct N=2048, N_T=64 FP32 pairs in one autotuned, graph-captured
+  persistent launch, launched back to back: every tile against the oracle;
+* the 64-pair mixed batch (N up to 8192, 7.9 GB) rendered on the device,
+  one autotuned launch: sampled tiles;
+* 16 pairs at N=8192, N_T=64 in FP16 and BF16, one launch: sampled tiles;
+* served requests at N=8192 and 16384 (FP16): sampled tiles.
+
+Sampled tiles are checked against the oracle on pixel windows that the host
+mirror of the device generator (synth.render_epoch_window) makes, bit for
+bit, so no oracle input comes from the CUDA path."""
+import math
+
+import numpy as np
+import pytest
+
+import parity
+from paper_2501_10653_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+PARAMS = {"C1": 1e-6, "C2": 1e-6, "C": 1e-6, "D": 0.0}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2501_10653_gb300 import build, iqa
+    build.build()
+    h = iqa.iqa_create(0, 0)
+    yield h
+    iqa.iqa_destroy(h)
+
+
+def _picks(T, rng, k):
+    return np.unique(np.concatenate([rng.integers(0, T * T, k),
+                                     [0, T - 1, T * T - T, T * T - 1]]))
+
+
+def _plan_run(ctx, pairs, code, tune_iters, launches):
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    st = torch.cuda.Stream()
+    plan = iqa.iqa_plan_create(ctx, pairs, code, PARAMS, iqa.IQA_PLAN_GRAPH)
+    try:
+        if tune_iters:
+            iqa.iqa_plan_autotune(plan, st, tune_iters)
+        with torch.cuda.stream(st):
+            for _ in range(launches):
+                iqa.iqa_plan_launch(plan, st)
+        torch.cuda.synchronize()
+        iqa.iqa_wait(ctx, st, 30_000_000)
+    finally:
+        iqa.iqa_plan_destroy(plan)
+
+
+def test_headline_configuration_every_tile(ctx, orc):
+    """bench.py's timed step: 32 distinct paper-scale pairs (the same seeded
+    inputs), one persistent launch, autotuned and replayed back to back."""
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    N, NT, B = 2048, 64, 32
+    T = N // NT
+    host = [synth.paper_pair(pair_index=i) for i in range(B)]
+    dev = [(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()) for x, y in host]
+    outs = [(torch.full((T * T,), float("nan"), device="cuda"),
+             torch.full((T * T,), float("nan"), device="cuda")) for _ in range(B)]
+    pairs = [iqa.make_pair(d[0], d[1], N, NT, o[0], o[1]) for d, o in zip(dev, outs)]
+    _plan_run(ctx, pairs, iqa.IQA_F32, 2, 5)
+    for (x, y), (lm, am) in zip(host, outs):
+        want = parity.oracle_maps(orc, x, y, NT, PARAMS)
+        parity.assert_parity((lm.cpu().numpy(), am.cpu().numpy(), None), want, PARAMS)
+
+
+def test_mixed_batch_full_size_sampled(ctx, orc):
+    """bench.py's mixed batch: 64 pairs, N in {1024..8192}, N_T in {32,64,128},
+    skies rendered on the device exactly as the bench renders them."""
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    specs = synth.mixed_batch_specs()
+    xs, ys, outs, pairs, meta = [], [], [], [], []
+    for i, (N, NT) in enumerate(specs):
+        cat = synth.serving_catalog(N, i, seed=2)
+        cat2 = synth.catalog_without_faintest(cat, int(math.ceil(0.1 * len(cat["x"]))))
+        x = torch.empty(N * N, device="cuda")
+        y = torch.empty(N * N, device="cuda")
+        iqa.iqa_render_epoch(ctx, cat, 2 * 10**6 + 2 * i, x, iqa.IQA_F32)
+        iqa.iqa_render_epoch(ctx, cat2, 2 * 10**6 + 2 * i + 1, y, iqa.IQA_F32)
+        T = N // NT
+        o = (torch.full((T * T,), float("nan"), device="cuda"),
+             torch.full((T * T,), float("nan"), device="cuda"))
+        xs.append(x)
+        ys.append(y)
+        outs.append(o)
+        pairs.append(iqa.make_pair(x, y, N, NT, *o))
+        meta.append((cat, cat2, 2 * 10**6 + 2 * i))
+    _plan_run(ctx, pairs, iqa.IQA_F32, 2, 2)
+    rng = np.random.default_rng(21)
+    for i, ((N, NT), o, (cat, cat2, seed)) in enumerate(zip(specs, outs, meta)):
+        T = N // NT
+        picks = _picks(T, rng, 4)
+        want = []
+        for t in picks:
+            r0, c0 = (t // T) * NT, (t % T) * NT
+            xw = synth.render_epoch_window(cat, seed, r0, r0 + NT, c0, c0 + NT)
+            yw = synth.render_epoch_window(cat2, seed + 1, r0, r0 + NT, c0, c0 + NT)
+            want.append(parity.oracle_tile(orc, xw, yw, PARAMS))
+        parity.assert_sampled(o[0].cpu().numpy(), o[1].cpu().numpy(), picks, want, PARAMS)
+    del xs, ys, outs
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dt", ["f16", "bf16"])
+def test_precision_size_16bit_batch_sampled(ctx, orc, dt):
+    """16 pairs at N=8192, N_T=64 stored in 16 bits, one persistent launch
+    (the precision workload's size and launch), noise sigma 5e-3."""
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    N, NT, B = 8192, 64, 16
+    T = N // NT
+    code = {"f16": iqa.IQA_F16, "bf16": iqa.IQA_BF16}[dt]
+    tdt = {"f16": torch.float16, "bf16": torch.bfloat16}[dt]
+    cats, outs, pairs, keep = [], [], [], []
+    for i in range(B):
+        cat = synth.serving_catalog(N, i, seed=3, noise=5e-3)
+        x = torch.empty(N * N, dtype=tdt, device="cuda")
+        y = torch.empty(N * N, dtype=tdt, device="cuda")
+        iqa.iqa_render_epoch(ctx, cat, 3 * 10**6 + 2 * i, x, code)
+        iqa.iqa_render_epoch(ctx, cat, 3 * 10**6 + 2 * i + 1, y, code, drop=[0, 1])
+        o = (torch.full((T * T,), float("nan"), device="cuda"),
+             torch.full((T * T,), float("nan"), device="cuda"))
+        cats.append(cat)
+        outs.append(o)
+        keep.append((x, y))
+        pairs.append(iqa.make_pair(x, y, N, NT, *o))
+    _plan_run(ctx, pairs, code, 0, 2)
+    rng = np.random.default_rng(33)
+    for i, (cat, o) in enumerate(zip(cats, outs)):
+        picks = _picks(T, rng, 6)
+        want = []
+        for t in picks:
+            r0, c0 = (t // T) * NT, (t % T) * NT
+            xw = synth.render_epoch_window(cat, 3 * 10**6 + 2 * i, r0, r0 + NT, c0, c0 + NT,
+                                           dtype=dt)
+            yw = synth.render_epoch_window(cat, 3 * 10**6 + 2 * i + 1, r0, r0 + NT, c0,
+                                           c0 + NT, drop=[0, 1], dtype=dt)
+            want.append(parity.oracle_tile(orc, xw, yw, PARAMS))
+        parity.assert_sampled(o[0].cpu().numpy(), o[1].cpu().numpy(), picks, want, PARAMS)
+    del keep, outs
+    torch.cuda.empty_cache()
+
+
+def test_served_requests_at_full_size_sampled(ctx, orc):
+    """The serving workload's largest sizes (N = 8192 and 16384, FP16), with
+    drops and transients, served in batched steps."""
+    import time
+    from paper_2501_10653_gb300 import iqa
+    srv = iqa.iqa_server_create(ctx, dtype=iqa.IQA_F16, max_pairs_per_step=8,
+                                max_inflight_steps=2, pool_bytes=4 << 30, params=PARAMS)
+    try:
+        cats = {}
+        for rid, N in ((0, 8192), (1, 16384)):
+            cats[rid] = synth.serving_catalog(N, rid)
+            iqa.iqa_server_add_reference(srv, rid, cats[rid], 900 + rid)
+        reqs = [(0, 64, 41, [0, 3], (2, 4000, 5000, 0.4)), (1, 128, 42, [1], None),
+                (1, 32, 43, [], (5, 16000, 300, 1.2)), (0, 32, 44, [2], None)]
+        hs = [iqa.iqa_submit(srv, iqa.make_request(r, nt, sd, dr, ad))
+              for r, nt, sd, dr, ad in reqs]
+        t0 = time.time()
+        for h in hs:
+            while iqa.iqa_poll(srv, h, 200_000) == iqa.IQA_PENDING:
+                assert time.time() - t0 < 120
+        rng = np.random.default_rng(44)
+        for h, (rid, NT, seed, drop, add) in zip(hs, reqs):
+            assert iqa.iqa_poll(srv, h, 0) == iqa.IQA_OK
+            cat = cats[rid]
+            N = cat["N"]
+            T = N // NT
+            lm = np.full(T * T, np.nan, np.float32)
+            am = np.full(T * T, np.nan, np.float32)
+            iqa.iqa_result(srv, h, lm, am)
+            picks = _picks(T, rng, 6)
+            if add is not None:  # the tile holding the transient's centre
+                picks = np.unique(np.append(picks, (add[2] // NT) * T + add[1] // NT))
+            want = []
+            for t in picks:
+                r0, c0 = (t // T) * NT, (t % T) * NT
+                xw = synth.render_epoch_window(cat, 900 + rid, r0, r0 + NT, c0, c0 + NT,
+                                               dtype="f16")
+                yw = synth.render_epoch_window(cat, seed, r0, r0 + NT, c0, c0 + NT, drop=drop,
+                                               add=add, dtype="f16")
+                want.append(parity.oracle_tile(orc, xw, yw, PARAMS))
+            parity.assert_sampled(lm, am, picks, want, PARAMS)
+    finally:
+        iqa.iqa_server_destroy(srv)
