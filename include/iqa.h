@@ -188,9 +188,12 @@ iqa_status iqa_both_host_many(iqa_ctx *ctx, const iqa_host_pair *pairs, int npai
  *
  * variant 1, the persistent TMA kernel: `ctas_per_sm` CTAs per SM loop over
  * units of `tiles_across` whole tiles; a producer warp streams each unit in
- * chunks with 2-D tensor copies into a ring of `stages` shared-memory stages of
- * `stage_kb` KB per image, and `threads` consumer threads reduce them.  Needs
- * 16-byte aligned images, NT a multiple of 16 bytes, tiles_across * NT <= 256.
+ * chunks with tensor copies (one 2-D box for a unit row of at most 256
+ * elements; one 3-D box of 256-element segments for a row of 512 or 1024
+ * elements when N is a multiple of 256) into a ring of `stages` shared-memory
+ * stages of `stage_kb` KB per image, and `threads` consumer threads reduce
+ * them.  Needs 16-byte aligned images, NT a multiple of 16 bytes, and
+ * tiles_across * NT <= 256, or 512 or 1024 with N a multiple of 256.
  *   threads        128, 256 or 512 consumer threads (plus one producer warp)
  *   tiles_across   whole tiles per unit (plans choose it per pair from
  *                  unit_kpx: the widest unit of at most unit_kpx K pixels)
