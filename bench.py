@@ -355,6 +355,50 @@ def precision_report(iqa, ctx, params, stream, batch=16):
     return out
 
 
+def merge_report(iqa, params, ctx, stream, x, y, K=200):
+    """Eq. 3 / Eq. 4 merging (Section 3) from the exported per-tile sums of
+    one N=2048, N_T=16 FP32 pair: merged maps at m = 2, 8 and the whole image
+    (m = 128), each against computing the same coarser map from the pixels
+    again (N_T' = m N_T); device time per call, back to back."""
+    import torch
+    N, NT = x.shape[0], 16
+    T = N // NT
+    sums = torch.empty((T * T, 4), dtype=torch.float64, device=x.device)
+    lm = torch.empty(T * T, device=x.device)
+    am = torch.empty(T * T, device=x.device)
+    iqa.iqa_both(ctx, x, y, iqa.IQA_F32, N, NT, params, lm, am, sums, stream)
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(5):
+                fn()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(K):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / K
+
+    out = {"workload": "one N=2048 FP32 pair, tile sums at N_T=16 (T=128)",
+           "tile_map_us": round(timed(lambda: iqa.iqa_both(ctx, x, y, iqa.IQA_F32, N, NT,
+                                                           params, lm, am, sums, stream)), 2)}
+    for m in (2, 8, T):
+        t = T // m
+        ml = torch.empty(t * t, device=x.device)
+        ma = torch.empty(t * t, device=x.device)
+        rl = torch.empty(t * t, device=x.device)
+        ra = torch.empty(t * t, device=x.device)
+        merge_us = timed(lambda: iqa.iqa_merge(ctx, sums, T, m, params, ml, ma, None, stream))
+        direct_us = timed(lambda: iqa.iqa_both(ctx, x, y, iqa.IQA_F32, N, NT * m, params, rl,
+                                               ra, None, stream))
+        out["m%d" % m] = {"merged_tiles": t * t, "merge_us": round(merge_us, 2),
+                          "from_pixels_us": round(direct_us, 2),
+                          "sums_bytes_read": T * T * 32}
+    return out
+
+
 SERVE_NS = (512, 1024, 2048, 4096, 8192, 16384)
 
 
@@ -592,6 +636,9 @@ def run_ours(args):
     prec = None
     if rank == 0 and world == 1 and not args.no_precision:
         prec = precision_report(iqa, ctx, params, stream, args.precision_batch)
+    merge = None
+    if rank == 0 and world == 1:
+        merge = merge_report(iqa, params, ctx, stream, dx[0], dy[0])
     mixed = None
     if rank == 0 and world == 1 and not args.no_mixed:
         mixed = mixed_batch_report(iqa, ctx, params, stream)
@@ -694,6 +741,7 @@ def run_ours(args):
                                    % info["config"]["threads"]},
             "cpu_baseline": cpu,
             "mixed_batch_64": mixed,
+            "merge_eq3_eq4": merge,
             "precision_N8192": prec,
             "serving": serve,
             "paper_context": PAPER_H100,

@@ -5,18 +5,65 @@
 // Eq. 3 multiplies each lisi_t by (max(Sx_t, Sy_t) + C2), which by Eq. 1 is
 // D * A_t; Eq. 4 multiplies each auglisi_t by (Sx_t + Sy_t + C), which by Eq. 2
 // is Sx_t + Sy_t + C - B_t, and removes the (n - 1) extra C.  Both therefore
-// equal Eq. 1 / Eq. 2 applied to the block's summed (A, B, Sx, Sy); the kernel
-// sums the four per-tile sums of each block in FP64, in a fixed order, and
-// applies Eq. 1 / Eq. 2 once.  The data is tiny (32 bytes per tile), so FP64
-// costs nothing here.
+// equal Eq. 1 / Eq. 2 applied to the block's summed (A, B, Sx, Sy); the kernels
+// sum the four per-tile sums of each block in FP64, in an order fixed by the
+// launch shape (so results repeat bit for bit), and apply Eq. 1 / Eq. 2 once.
+//
+// The work is m^2 tiles of 32 bytes per merged tile, so the launch shape
+// follows m: one thread per merged tile for small blocks, one warp for
+// middling ones, and for large blocks (up to the whole image) a cluster of
+// kClusterCtas CTAs whose partial sums meet in distributed shared memory.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "iqa.h"
 #include "iqa_ctx.h"
 
+namespace cg = cooperative_groups;
+
 namespace iqa {
 
 constexpr int kMergeThreads = 256;
+constexpr int kClusterCtas = 8;
+constexpr long long kThreadMaxTiles = 16;    // m^2 <= 16: one thread per merged tile
+constexpr long long kWarpMaxTiles = 8192;    // m^2 <= 8192: one warp per merged tile
+
+struct MergeArgs {
+    const double *sums;
+    int T, m, M;  // tiles per row, merge factor, merged tiles per row
+    double C2, C, D;
+    float *lisi;
+    float *aug;
+    double *out_sums;
+};
+
+__device__ __forceinline__ void add4(double (&s)[4], const double *p)
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s[k] += p[k];
+}
+
+// Tile i (row-major) of merged tile b.
+__device__ __forceinline__ const double *tile_of(const MergeArgs &a, long long b, long long i)
+{
+    const long long R = b / a.M, Cc = b - R * a.M;
+    const long long r = R * a.m + i / a.m, c = Cc * a.m + i % a.m;
+    return a.sums + 4 * (r * a.T + c);
+}
+
+__device__ __forceinline__ void write_merged(const MergeArgs &a, long long b, const double (&t)[4])
+{
+    const double A = t[0], B = t[1], Sx = t[2], Sy = t[3];
+    if (a.lisi) a.lisi[b] = (float)(a.D * A / (fmax(Sx, Sy) + a.C2));
+    if (a.aug) a.aug[b] = (float)(1.0 - B / (Sx + Sy + a.C));
+    if (a.out_sums) {
+        double *o = a.out_sums + 4 * b;
+        o[0] = A;
+        o[1] = B;
+        o[2] = Sx;
+        o[3] = Sy;
+    }
+}
 
 __device__ __forceinline__ double warp_sum_d(double v)
 {
@@ -25,50 +72,71 @@ __device__ __forceinline__ double warp_sum_d(double v)
     return v;
 }
 
-// One CTA per merged tile: threads stride over the block's m*m tiles (row-
-// major), then a shuffle tree and shared memory combine them.
-__global__ void __launch_bounds__(kMergeThreads)
-    iqa_merge_kernel(const double *__restrict__ sums, int T, int m, double C2, double C,
-                     double D, float *__restrict__ lisi, float *__restrict__ aug,
-                     double *__restrict__ out_sums)
+// m^2 <= kThreadMaxTiles: thread b sums its block's tiles row by row.
+__global__ void __launch_bounds__(kMergeThreads) iqa_merge_thread_kernel(MergeArgs a)
+{
+    const long long b = (long long)blockIdx.x * kMergeThreads + threadIdx.x;
+    if (b >= (long long)a.M * a.M) return;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    const long long n = (long long)a.m * a.m;
+    for (long long i = 0; i < n; ++i) add4(s, tile_of(a, b, i));
+    write_merged(a, b, s);
+}
+
+// m^2 <= kWarpMaxTiles: warp b takes its block's tiles lane-strided, then an
+// xor-shuffle tree.
+__global__ void __launch_bounds__(kMergeThreads) iqa_merge_warp_kernel(MergeArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const long long b = ((long long)blockIdx.x * kMergeThreads + threadIdx.x) >> 5;
+    if (b >= (long long)a.M * a.M) return;  // whole warps leave together
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    const long long n = (long long)a.m * a.m;
+    for (long long i = lane; i < n; i += 32) add4(s, tile_of(a, b, i));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s[k] = warp_sum_d(s[k]);
+    if (lane == 0) write_merged(a, b, s);
+}
+
+// Larger blocks: cluster b (kClusterCtas CTAs) takes merged tile b; CTA rank
+// q sums the tiles i = q * kMergeThreads + tid + j * kClusterCtas *
+// kMergeThreads, reduces them in shared memory, and rank 0 adds the ranks'
+// partials in rank order through distributed shared memory.
+__global__ void __launch_bounds__(kMergeThreads) iqa_merge_cluster_kernel(MergeArgs a)
 {
     __shared__ double red[4][kMergeThreads / 32];
-    const int M = T / m;
-    const int R = blockIdx.x / M, Cc = blockIdx.x % M;
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
-    const long long count = (long long)m * m;
-    for (long long i = threadIdx.x; i < count; i += kMergeThreads) {
-        const long long r = (long long)R * m + i / m;
-        const long long c = (long long)Cc * m + i % m;
-        const double *p = sums + 4 * (r * T + c);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) s[k] += p[k];
-    }
+    __shared__ double part[4];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int q = (int)cluster.block_rank();
+    const long long b = blockIdx.x / kClusterCtas;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    const long long n = (long long)a.m * a.m;
+    const long long step = (long long)kClusterCtas * kMergeThreads;
+    for (long long i = (long long)q * kMergeThreads + threadIdx.x; i < n; i += step)
+        add4(s, tile_of(a, b, i));
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        double v = warp_sum_d(s[k]);
+        const double v = warp_sum_d(s[k]);
         if (lane == 0) red[k][warp] = v;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            t[k] = 0.0;
-            for (int w = 0; w < kMergeThreads / 32; ++w) t[k] += red[k][w];
-        }
-        const double A = t[0], B = t[1], Sx = t[2], Sy = t[3];
-        if (lisi) lisi[blockIdx.x] = (float)(D * A / (fmax(Sx, Sy) + C2));
-        if (aug) aug[blockIdx.x] = (float)(1.0 - B / (Sx + Sy + C));
-        if (out_sums) {
-            double *o = out_sums + 4 * (long long)blockIdx.x;
-            o[0] = A;
-            o[1] = B;
-            o[2] = Sx;
-            o[3] = Sy;
-        }
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int w = 0; w < kMergeThreads / 32; ++w) t += red[threadIdx.x][w];
+        part[threadIdx.x] = t;
     }
+    cluster.sync();
+    if (q == 0 && threadIdx.x == 0) {
+        double t[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int r = 0; r < kClusterCtas; ++r) {
+            const double *rp = cluster.map_shared_rank(part, r);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) t[k] += rp[k];
+        }
+        write_merged(a, b, t);
+    }
+    cluster.sync();  // keep every rank's shared memory alive until read
 }
 
 }  // namespace iqa
@@ -89,15 +157,37 @@ extern "C" iqa_status iqa_merge(iqa_ctx *ctx, const double *sums, int T, int m,
         return IQA_ERR_INVALID_ARG;
     }
     const long long M = T / m;
-    if (M * M > 0x7fffffffLL) {
+    const long long n = (long long)m * m;
+    if (M * M * kClusterCtas > 0x7fffffffLL) {
         set_error(ctx, "too many merged tiles");
         return IQA_ERR_UNSUPPORTED;
     }
     iqa_params P;
     iqa_status s = resolve_params(ctx, params, &P);
     if (s != IQA_OK) return s;
-    iqa_merge_kernel<<<(unsigned)(M * M), kMergeThreads, 0, (cudaStream_t)stream>>>(
-        sums, T, m, P.C2, P.C, P.D, merged_lisi, merged_aug, merged_sums);
+    MergeArgs a{sums, T, m, (int)M, P.C2, P.C, P.D, merged_lisi, merged_aug, merged_sums};
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n <= kThreadMaxTiles) {
+        const long long blocks = (M * M + kMergeThreads - 1) / kMergeThreads;
+        iqa_merge_thread_kernel<<<(unsigned)blocks, kMergeThreads, 0, st>>>(a);
+    } else if (n <= kWarpMaxTiles) {
+        const long long blocks = (M * M * 32 + kMergeThreads - 1) / kMergeThreads;
+        iqa_merge_warp_kernel<<<(unsigned)blocks, kMergeThreads, 0, st>>>(a);
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        cfg.gridDim = dim3((unsigned)(M * M * kClusterCtas));
+        cfg.blockDim = dim3(kMergeThreads);
+        cfg.stream = st;
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kClusterCtas;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelEx(&cfg, iqa_merge_cluster_kernel, a);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "merge kernel launch");
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "merge kernel launch");
     return IQA_OK;

@@ -319,7 +319,10 @@ def test_tma_kernel_single_maps(ctx, orc, paper, which):
     parity.assert_parity(got, want, PARAMS)
 
 
-@pytest.mark.parametrize("NT,m", [(16, 2), (16, 8), (32, 4), (64, 32), (64, 1), (128, 16)])
+# m^2 <= 16: a thread per merged tile; <= 8192: a warp; larger (whole image at
+# N_T = 16: 16384 tiles; 4 blocks of 4096 at m = 64 use warps): an 8-CTA cluster
+@pytest.mark.parametrize("NT,m", [(16, 2), (16, 8), (32, 4), (64, 32), (64, 1), (128, 16),
+                                  (16, 64), (16, 128), (8, 256), (8, 128)])
 def test_merge_eq3_eq4_against_oracle(ctx, orc, paper, NT, m):
     """Eq. 3 / Eq. 4 merging of m x m tile blocks (m = T: the whole image) from
     the GPU's per-tile sums, against the oracle's merge (Eq. 3 / Eq. 4 in the
@@ -346,6 +349,27 @@ def test_merge_eq3_eq4_against_oracle(ctx, orc, paper, NT, m):
     r = direct[2][:, 1] / (direct[2][:, 2] + direct[2][:, 3] + PARAMS["C"])
     parity.assert_lisi_close(got[0], el.ravel())
     parity.assert_aug_close(got[1], ea.ravel(), r)
+
+
+def test_merge_repeats_bit_for_bit(ctx, paper):
+    """Every merge shape sums in an order fixed by the launch: repeated calls
+    agree bit for bit."""
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    x, y = paper
+    NT = 8
+    T = 2048 // NT
+    _, _, sums = parity.gpu_maps(ctx, x, y, NT, PARAMS)
+    ds = torch.from_numpy(sums).cuda()
+    for m in (2, 16, 256):
+        M = T // m
+        outs = []
+        for _ in range(3):
+            ms = torch.empty((M * M, 4), device="cuda", dtype=torch.float64)
+            iqa.iqa_merge(ctx, ds, T, m, PARAMS, None, None, ms, torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            outs.append(ms.cpu().numpy())
+        assert all(np.array_equal(outs[0].view(np.uint64), o.view(np.uint64)) for o in outs)
 
 
 def test_merge_rejects_bad_factor(ctx):
