@@ -223,6 +223,10 @@ __global__ void __launch_bounds__(CT + 32, 1)
             mbar_init(&empty[s], CT / 32);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // programmatic dependent launch: the next kernel in the stream may be
+        // scheduled once every CTA of this one is resident; it waits (below,
+        // griddepcontrol.wait) for this grid to finish before touching memory
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     }
     __syncthreads();
 
@@ -236,14 +240,17 @@ __global__ void __launch_bounds__(CT + 32, 1)
         // atomicAdd on the shared counter per grab, issued one grab ahead so
         // that its latency hides behind the current grab's copies.  A grab
         // spans about kGrabBytes of each image (several small units, or one).
+        // The first unit of every CTA is its own index (no atomic on the
+        // launch's critical path); dynamic grabs then count from gridDim.x,
+        // and shrink toward one unit as the work runs out (guided), so that
+        // the CTAs finish close together.
         constexpr uint32_t kGrabBytes = 65536;
         long long u = blockIdx.x, u_end = u + 1, nxt = -1, nxt_end = -1, i = 0;
         bool have_next = false;
+        // a kernel earlier in the stream (programmatic dependent launch) may
+        // still be running: wait for it before any work is fetched or copied
+        asm volatile("griddepcontrol.wait;" ::: "memory");
         if (sp.inject_stall) ok = false;  // test hook: issue nothing at all
-        else if (sp.sched) {
-            u = (long long)atomicAdd(&sp.sched[0], 1ull);
-            u_end = u + 1;
-        }
         // pair of unit u: units are taken in increasing order, so the pair
         // index only moves forward (a binary search only when u passes the
         // next pair's first unit)
@@ -283,9 +290,12 @@ __global__ void __launch_bounds__(CT + 32, 1)
                 if (!have_next) {
                     if (sp.sched) {
                         const uint32_t unit_bytes = bytes * (uint32_t)d.chunks;
-                        const unsigned g =
+                        unsigned g =
                             unit_bytes >= kGrabBytes ? 1u : min(8u, kGrabBytes / unit_bytes);
-                        nxt = (long long)atomicAdd(&sp.sched[0], (unsigned long long)g);
+                        const long long share = (total_units - u) / (4LL * gridDim.x);
+                        if (share < (long long)g) g = (unsigned)(share > 1 ? share : 1);
+                        nxt = (long long)gridDim.x +
+                              (long long)atomicAdd(&sp.sched[0], (unsigned long long)g);
                         nxt_end = nxt + g;
                     } else {
                         nxt = blockIdx.x + (++i) * (long long)gridDim.x;

@@ -25,7 +25,14 @@ static cudaError_t stream_launch_one(const StreamParams &sp, int grid, size_t sm
     cfg.blockDim = dim3(CT + 32, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cfg.numAttrs = 0;
+    // programmatic dependent launch: the kernel may start while the previous
+    // kernel in the stream finishes; it waits for it (griddepcontrol.wait)
+    // before reading work or pixels
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, sp);
 }
 
