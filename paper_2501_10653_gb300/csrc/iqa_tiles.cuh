@@ -22,6 +22,12 @@ __global__ void __launch_bounds__(THREADS)
     __shared__ float red[4][THREADS];
     __shared__ float part[kMaxTX * 4];
 
+    // programmatic dependent launch: let the next kernel in the stream be
+    // scheduled as this grid drains, and wait for the previous one (which may
+    // have written these images or maps) before the first access
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+
     const int tile_col0 = blockIdx.x * p.TX;
     const int srank = blockIdx.y % p.S;
     const int tile_row = p.tile_row0 + blockIdx.y / p.S;
@@ -68,15 +74,17 @@ static cudaError_t launch_one(const TileArgs &p, int rows, cudaStream_t st)
     cfg.blockDim = dim3(THREADS, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    cfg.numAttrs = 0;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     if (p.S > 1) {
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 1;
-        attr[0].val.clusterDim.y = (unsigned)p.S;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        attr[1].id = cudaLaunchAttributeClusterDimension;
+        attr[1].val.clusterDim.x = 1;
+        attr[1].val.clusterDim.y = (unsigned)p.S;
+        attr[1].val.clusterDim.z = 1;
+        cfg.numAttrs = 2;
     }
     return cudaLaunchKernelEx(&cfg, iqa_tiles_kernel<T, VEC, ILP, THREADS, DO_A, DO_B>, p);
 }
