@@ -54,8 +54,8 @@ PROFILED_TRAFFIC = {
                 "paper_2501_10653_gb300/csrc/iqa_stream.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream_launch.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream_f32.cu"],
-    "sha256": "8c30136b67afc3a07f89b299d30c97cf620506a52de4872ce6d8994ca214dd3d",
-    "bytes_per_pair": (268492800 + 3802368) / 8,
+    "sha256": "464694329a4d909c2138c0ade45edf9e69aa2683902e2331f93cd0b4ac780963",
+    "bytes_per_pair": (268508160 + 4065280) / 8,
     "capture": "8 pairs per launch, scaled by pairs to the timed launch",
 }
 PAPER_H100 = {"lisi_kernel_ms": 0.101, "auglisi_kernel_ms": 0.091,
@@ -74,6 +74,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="bound on the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-merge", action="store_true",
+                    help="skip the Eq. 3 / Eq. 4 merge report")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the N=8192 FP32/FP16/BF16 precision and throughput report")
     ap.add_argument("--no-mixed", action="store_true",
@@ -646,7 +648,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_precision:
         prec = precision_report(iqa, ctx, params, stream, args.precision_batch)
     merge = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_merge:
         merge = merge_report(iqa, params, ctx, stream, dx[0], dy[0])
     mixed = None
     if rank == 0 and world == 1 and not args.no_mixed:
