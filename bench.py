@@ -52,9 +52,8 @@ PAPER_NT_SWEEP = (16, 32, 64, 128, 256)
 PROFILED_TRAFFIC = {
     "sources": ["paper_2501_10653_gb300/csrc/iqa_device.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream.cuh",
-                "paper_2501_10653_gb300/csrc/iqa_stream_launch.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream_f32.cu"],
-    "sha256": "464694329a4d909c2138c0ade45edf9e69aa2683902e2331f93cd0b4ac780963",
+    "sha256": "c4c9cb716c3f51c596e0858d7e9f642790580fd75afd3ef77b7f63f050d4ee7e",
     "bytes_per_pair": (268508160 + 4065280) / 8,
     "capture": "8 pairs per launch, scaled by pairs to the timed launch",
 }

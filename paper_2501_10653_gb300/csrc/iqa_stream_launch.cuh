@@ -2,6 +2,9 @@
 // storage type (included by iqa_stream_<type>.cu).
 #pragma once
 
+#include <atomic>
+#include <mutex>
+
 #include "iqa_internal.h"
 #include "iqa_stream.cuh"
 
@@ -12,13 +15,19 @@ static cudaError_t stream_launch_one(const StreamParams &sp, int grid, size_t sm
                                      cudaStream_t st)
 {
     auto kern = iqa_stream_kernel<T, CT, A, B>;
-    // raise the dynamic shared-memory limit once per instantiation
-    static size_t allowed = 0;
-    if (smem > allowed) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        allowed = smem;
+    // raise the dynamic shared-memory limit when a launch needs more than any
+    // earlier one of this instantiation; host threads may launch concurrently,
+    // so raises are serialised and the limit only ever grows
+    static std::atomic<size_t> allowed{0};
+    static std::mutex raise_mu;
+    if (smem > allowed.load(std::memory_order_acquire)) {
+        std::lock_guard<std::mutex> g(raise_mu);
+        if (smem > allowed.load(std::memory_order_relaxed)) {
+            cudaError_t e = cudaFuncSetAttribute(
+                kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            allowed.store(smem, std::memory_order_release);
+        }
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid, 1, 1);
