@@ -22,6 +22,13 @@
  *   - Device-pointer calls are stream-ordered: they validate, enqueue on the
  *     given stream and return without synchronising.  The stream must belong
  *     to the context's device, and that device must be current.
+ *   - The map kernels use programmatic dependent launch: each may be
+ *     scheduled while the previous kernel in the stream drains, and waits for
+ *     it before its first memory access; each lets the next kernel start
+ *     early.  A caller's own kernel that follows on the stream with
+ *     programmatic stream serialization enabled must wait for its prerequisite
+ *     grid (griddepcontrol.wait) before reading the maps; any other work
+ *     follows in plain stream order.
  *   - Nothing throws across the ABI: every call returns an iqa_status, and
  *     iqa_last_error() gives a one-line reason for the latest failure.
  *   - The caller owns every buffer it passes; the context owns its workspace.
