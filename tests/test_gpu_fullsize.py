@@ -194,3 +194,53 @@ def test_served_requests_at_full_size_sampled(ctx, orc):
             parity.assert_sampled(lm, am, picks, want, PARAMS)
     finally:
         iqa.iqa_server_destroy(srv)
+
+
+def test_largest_image_both_kernels_sampled(ctx, orc):
+    """N = 32768 FP32 (8 GB per pair, 2^30 pixels per image, 262144 tiles at
+    N_T = 64): the one-pair kernel and a one-pair persistent plan agree bit for
+    bit on every tile, and sampled tiles match the oracle; N_T = N (one tile of
+    the whole image, split over a cluster) matches it too."""
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    N, NT = 32768, 64
+    T = N // NT
+    cat = synth.serving_catalog(N, 7, seed=5)
+    x = torch.empty(N * N, device="cuda")
+    y = torch.empty(N * N, device="cuda")
+    iqa.iqa_render_epoch(ctx, cat, 5001, x, iqa.IQA_F32)
+    iqa.iqa_render_epoch(ctx, cat, 5002, y, iqa.IQA_F32, drop=[0, 1, 2], add=(3, 20000, 777, 0.9))
+    st = torch.cuda.current_stream()
+    l1 = torch.full((T * T,), float("nan"), device="cuda")
+    a1 = torch.full((T * T,), float("nan"), device="cuda")
+    iqa.iqa_both(ctx, x, y, iqa.IQA_F32, N, NT, PARAMS, l1, a1, None, st)
+    l2 = torch.full((T * T,), float("nan"), device="cuda")
+    a2 = torch.full((T * T,), float("nan"), device="cuda")
+    _plan_run(ctx, [iqa.make_pair(x, y, N, NT, l2, a2)], iqa.IQA_F32, 0, 1)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(55)
+    picks = np.unique(np.append(_picks(T, rng, 12), (777 // NT) * T + 20000 // NT))
+    want = []
+    for t in picks:
+        r0, c0 = (t // T) * NT, (t % T) * NT
+        xw = synth.render_epoch_window(cat, 5001, r0, r0 + NT, c0, c0 + NT)
+        yw = synth.render_epoch_window(cat, 5002, r0, r0 + NT, c0, c0 + NT, drop=[0, 1, 2],
+                                       add=(3, 20000, 777, 0.9))
+        want.append(parity.oracle_tile(orc, xw, yw, PARAMS))
+    for lm, am in ((l1, a1), (l2, a2)):
+        parity.assert_sampled(lm.cpu().numpy(), am.cpu().numpy(), picks, want, PARAMS)
+    # the two kernels sum in different orders: equal within the parity bound
+    parity.assert_lisi_close(l2.cpu().numpy(), l1.cpu().numpy().astype(np.float64))
+    # one tile of the whole image: the sums against the sums of all 64-tiles
+    s_all = torch.empty((T * T, 4), dtype=torch.float64, device="cuda")
+    iqa.iqa_both(ctx, x, y, iqa.IQA_F32, N, NT, PARAMS, l1, a1, s_all, st)
+    s_one = torch.empty((1, 4), dtype=torch.float64, device="cuda")
+    lw = torch.empty(1, device="cuda")
+    aw = torch.empty(1, device="cuda")
+    iqa.iqa_both(ctx, x, y, iqa.IQA_F32, N, N, PARAMS, lw, aw, s_one, st)
+    torch.cuda.synchronize()
+    tot = s_all.cpu().numpy().sum(axis=0)
+    one = s_one.cpu().numpy()[0]
+    assert np.all(np.abs(one - tot) <= 1e-5 * np.abs(tot))
+    del x, y, l1, a1, l2, a2, s_all
+    torch.cuda.empty_cache()
