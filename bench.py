@@ -53,7 +53,7 @@ PROFILED_TRAFFIC = {
     "sources": ["paper_2501_10653_gb300/csrc/iqa_device.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream_f32.cu"],
-    "sha256": "c4c9cb716c3f51c596e0858d7e9f642790580fd75afd3ef77b7f63f050d4ee7e",
+    "sha256": "998b8d9e548593b748c7eda947a53d4d4520103e7999db9f6366b18f7de680f2",
     "bytes_per_pair": (268508160 + 4065280) / 8,
     "capture": "8 pairs per launch, scaled by pairs to the timed launch",
 }

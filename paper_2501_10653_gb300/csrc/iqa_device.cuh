@@ -9,9 +9,10 @@
 // thread block per tile with a shared-memory reduction.  Here a CTA streams a
 // "unit": a rectangle of RH rows and TX whole tiles across (or, with a cluster
 // of S CTAs along y, 1/S of one tile's rows), with 16-byte non-caching loads,
-// the clamp and every term fused into that single read, per-thread FP32 sums
-// folded with Kahan compensation, an FP32 shuffle-tree / cross-CTA combine,
-// and the per-tile ratios of Eq. 1 / Eq. 2 (FP64 where augLISI cancels).
+// the clamp and every term fused into that single read, packed f32x2 running
+// sums per thread over a pass of vectors, Kahan-compensated across passes, an
+// FP32 shuffle-tree / cross-CTA combine, and the per-tile ratios of Eq. 1 /
+// Eq. 2 (FP64 where augLISI cancels).
 #pragma once
 
 #include <cuda_bf16.h>

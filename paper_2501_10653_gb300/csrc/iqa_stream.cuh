@@ -2,17 +2,24 @@
 //
 // Same method as iqa_tiles.cuh (arxiv 2501.10653, Section 2, Eq. 1 and Eq. 2:
 // clamp, tile, four per-tile sums, per-tile ratios), laid out for GB300:
-//   * one CTA per SM slot loops over units (TX whole tiles across x N_T rows)
-//     of one or many image pairs, fetched from a global counter (dynamic) or
-//     taken round-robin (static); the producer tells the consumers which unit
-//     a stage holds through a per-stage slot in shared memory;
-//   * a producer warp streams every unit in chunks of CH rows with 2-D TMA
-//     tensor copies (cp.async.bulk.tensor) of x and y into a ring of shared-
+//   * one CTA per SM slot loops over units (TX whole tiles across x N_T rows,
+//     up to 1024 elements wide) of one or many image pairs: its own index
+//     first, then grabs of consecutive units from a global counter (about
+//     64 KB per image each, fetched one grab ahead, shrinking toward one unit
+//     as the work runs out), or round-robin without a counter; the producer
+//     tells the consumers which unit and pair a stage holds through per-stage
+//     slots in shared memory;
+//   * a producer warp streams every unit in chunks of CH rows with TMA tensor
+//     copies (cp.async.bulk.tensor: one 2-D box, or one 3-D box of 256-element
+//     segments for rows wider than 256) of x and y into a ring of shared-
 //     memory stages, signalling completion on per-stage mbarriers;
 //   * consumer warps read each stage with 16-byte shared loads, clamp, form
 //     the terms, accumulate in registers across the unit's chunks, release the
 //     stage, and reduce the unit (shuffle trees, a named barrier) while the
-//     producer is already several chunks ahead;
+//     producer is already a stage ahead;
+//   * launches use programmatic dependent launch: the next kernel in the
+//     stream may be scheduled while this one drains, and the producer waits
+//     for the previous grid before it fetches work or issues a copy;
 //   * every mbarrier wait is bounded by a time limit: on expiry the CTA
 //     records an error code, stops issuing, waits (bounded) for the copies it
 //     has in flight and returns, so the host sees a status instead of a hang.

@@ -4,7 +4,9 @@
 // Grid: x = unit column (TX whole tiles each), y = tile row * S + part, where a
 // tile taller than one unit is split over S CTAs that form a thread-block
 // cluster along y; the S partial sums meet in distributed shared memory and
-// the cluster's rank-0 CTA writes the tile.  Included once per storage type.
+// the cluster's rank-0 CTA writes the tile.  Launched with programmatic
+// dependent launch: every CTA waits for the previous grid in the stream before
+// its first access.  Included once per storage type.
 #pragma once
 
 #include <cooperative_groups.h>
