@@ -643,6 +643,25 @@ def run_ours(args):
         sweep[str(nt)] = round(max(10, min(K, 200)) * B * pair_bytes / (ms * 1e-3) / 1e9, 1)
         iqa.iqa_plan_destroy(pl)
 
+    # the same step with the pairs stored in 16 bits (rounded to nearest):
+    # half the bytes per pixel pair, so the rate in pixel pairs is the figure
+    # to compare
+    storage16 = {}
+    for name, code, tdt in (("f16", iqa.IQA_F16, torch.float16),
+                            ("bf16", iqa.IQA_BF16, torch.bfloat16)):
+        hx16 = [t.to(tdt) for t in dx]
+        hy16 = [t.to(tdt) for t in dy]
+        pairs16 = [iqa.make_pair(hx16[i], hy16[i], N, NT, lisi[i], aug[i]) for i in range(B)]
+        pl16 = iqa.iqa_plan_create(ctx, pairs16, code, params, 0)
+        K16 = max(10, min(K, 2000))
+        ms = _time_plan(iqa, ctx, pl16, stream, K16, 3)
+        iqa.iqa_plan_destroy(pl16)
+        storage16[name] = {
+            "GBs": round(K16 * B * pair_bytes / 2 / (ms * 1e-3) / 1e9, 1),
+            "pixel_pairs_per_s": round(K16 * B * N * N / (ms * 1e-3), 1),
+            "us_per_pair": round(ms * 1e3 / (K16 * B), 3)}
+        del hx16, hy16
+
     prec = None
     if rank == 0 and world == 1 and not args.no_precision:
         prec = precision_report(iqa, ctx, params, stream, args.precision_batch)
@@ -735,6 +754,7 @@ def run_ours(args):
                           "times are quantised to about 2 us on this GPU, so the mean of 60 "
                           "is the finer figure"},
             "nt_sweep_GBs": sweep,
+            "storage_16bit": storage16,
             "clocks": clk,
             "e2e": {"value": round(e2e_value, 2), "unit": "GB/s",
                     "h2d_bytes_per_step": B * pair_bytes,
