@@ -143,8 +143,9 @@ static iqa_status plan_capture(iqa_plan *pl)
 
 // Batched-kernel shape when nothing was tuned: the autotuner's usual choice on
 // GB300 (three CTAs per SM, each a 128-thread consumer group with a two-stage
-// ring of 16 KB per image).
-TileConfig default_batch_config()
+// ring of 16 KB per image), with units of 16K pixel pairs for FP32 and 32K for
+// 16-bit storage (the same bytes per unit).
+TileConfig default_batch_config(iqa_dtype dtype)
 {
     TileConfig c;
     c.variant = 1;
@@ -152,7 +153,7 @@ TileConfig default_batch_config()
     c.stages = 2;
     c.stage_kb = 16;
     c.ctas_per_sm = 3;
-    c.unit_kpx = 16;
+    c.unit_kpx = elem_size(dtype) == 2 ? 32 : 16;
     return c;
 }
 
@@ -225,7 +226,7 @@ iqa_status iqa_plan_create(iqa_ctx *ctx, const iqa_pair *pairs, int npairs, iqa_
         cudaSetDevice(prev);
         return IQA_ERR_NOMEM;
     }
-    TileConfig cfg = default_batch_config();
+    TileConfig cfg = default_batch_config(dtype);
     {
         std::lock_guard<std::mutex> g(ctx->cfg_mu);
         if (ctx->has_batch_cfg[dtype]) cfg = ctx->batch_cfg[dtype];
@@ -302,7 +303,8 @@ iqa_status iqa_plan_autotune(iqa_plan *plan, iqa_stream stream, int iters,
     const int shape_c[][4] = {{3, 16, 2, 16}, {2, 16, 2, 16}, {2, 16, 2, 4},
                               {3, 16, 2, 4},  {6, 8, 2, 4},   {4, 8, 3, 4},
                               {2, 16, 3, 4},  {4, 16, 1, 16}, {8, 8, 1, 4},
-                              {3, 8, 4, 4},   {2, 8, 4, 4},   {2, 16, 3, 16}};
+                              {3, 8, 4, 4},   {2, 8, 4, 4},   {2, 16, 3, 16},
+                              {2, 16, 3, 32}, {3, 16, 2, 32}};
     iqa_status s = IQA_OK;
     for (int th : threads_c) {
         for (const auto &sh : shape_c) {

@@ -19,7 +19,7 @@
 #include "iqa_stream.cuh"
 
 namespace iqa {
-TileConfig default_batch_config();
+TileConfig default_batch_config(iqa_dtype dtype);
 }
 
 using namespace iqa;
@@ -122,7 +122,7 @@ extern "C" iqa_status iqa_batch_noalloc(const iqa_pair *pairs, int npairs, iqa_d
     for (int i = 0; i < npairs; ++i) order[i] = i;
     std::stable_sort(order, order + npairs,
                      [&](int a, int b) { return pairs[a].NT > pairs[b].NT; });
-    TileConfig cfg = default_batch_config();
+    TileConfig cfg = default_batch_config(dtype);
     long long units = 0;
     int maps = 0;
     for (int k = 0; k < npairs; ++k) {

@@ -32,7 +32,7 @@
 #include "iqa_synth.h"
 
 namespace iqa {
-TileConfig default_batch_config();
+TileConfig default_batch_config(iqa_dtype dtype);
 }
 
 using namespace iqa;
@@ -780,7 +780,7 @@ iqa_status iqa_server_create(iqa_ctx *ctx, const iqa_server_config *cfg, iqa_ser
     srv->ctx = ctx;
     srv->cfg = *cfg;
     srv->P = P;
-    srv->kcfg = default_batch_config();
+    srv->kcfg = default_batch_config(cfg->dtype);
     srv->es = elem_size(cfg->dtype);
     srv->step_timeout_ms = cfg->step_timeout_ms > 0 ? cfg->step_timeout_ms : 10000.0;
     srv->pool.reset(cfg->pool_bytes);
