@@ -531,6 +531,17 @@ typedef enum {
     IQA_OPT_INJECT_STALL = 2
 } iqa_option;
 
+/*
+ * Checked build only (libiqa_checked.so, compiled with IQA_CHECKS=1): every
+ * kernel checks the geometry of each access -- unit and tile bounds, tensor
+ * copy coordinates and their 16-byte alignment, stage capacity, output tile
+ * indices, generator pixel indices -- counts each failed check and skips the
+ * access.  Synchronises the current device, returns the number of failed
+ * checks since the previous call in *count, and resets it.  The product
+ * library compiles no checks and returns IQA_ERR_UNSUPPORTED.
+ */
+iqa_status iqa_debug_violations(unsigned long long *count);
+
 /* Sets a context option.  Errors: IQA_ERR_INVALID_ARG (unknown option or
  * value out of range: the timeout must be 1 us .. 60 s). */
 iqa_status iqa_set_option(iqa_ctx *ctx, int option, long long value);

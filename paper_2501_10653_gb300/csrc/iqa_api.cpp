@@ -491,6 +491,34 @@ iqa_status iqa_set_option(iqa_ctx *ctx, int option, long long value)
     }
 }
 
+#if IQA_CHECKS
+extern "C" unsigned int iqa_read_violations_tiles_f32();
+extern "C" unsigned int iqa_read_violations_tiles_f16();
+extern "C" unsigned int iqa_read_violations_tiles_bf16();
+extern "C" unsigned int iqa_read_violations_stream_f32();
+extern "C" unsigned int iqa_read_violations_stream_f16();
+extern "C" unsigned int iqa_read_violations_stream_bf16();
+extern "C" unsigned int iqa_read_violations_synth();
+extern "C" unsigned int iqa_read_violations_merge();
+#endif
+
+iqa_status iqa_debug_violations(unsigned long long *count)
+{
+    if (!count) return IQA_ERR_INVALID_ARG;
+    *count = 0;
+#if IQA_CHECKS
+    cudaDeviceSynchronize();
+    *count = (unsigned long long)iqa_read_violations_tiles_f32() +
+             iqa_read_violations_tiles_f16() + iqa_read_violations_tiles_bf16() +
+             iqa_read_violations_stream_f32() + iqa_read_violations_stream_f16() +
+             iqa_read_violations_stream_bf16() + iqa_read_violations_synth() +
+             iqa_read_violations_merge();
+    return IQA_OK;
+#else
+    return IQA_ERR_UNSUPPORTED;
+#endif
+}
+
 iqa_status iqa_wait(iqa_ctx *ctx, iqa_stream stream, int timeout_us)
 {
     if (!ctx) return IQA_ERR_INVALID_ARG;

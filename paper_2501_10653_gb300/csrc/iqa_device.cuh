@@ -20,6 +20,37 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// Bounds checks of the checked build (IQA_CHECKS=1, libiqa_checked.so): every
+// kernel checks the geometry of what it is about to read or write (unit and
+// tile bounds, TMA box coordinates, stage capacity, output indices) with
+// IQA_CHECK(cond); a failed check counts one violation in this translation
+// unit's device counter and the access is skipped (nothing traps).  In the
+// product build IQA_CHECK(cond) is `true` and the condition is not compiled.
+#ifndef IQA_CHECKS
+#define IQA_CHECKS 0
+#endif
+#if IQA_CHECKS
+static __device__ unsigned int g_iqa_violations;
+__device__ __forceinline__ bool iqa_check_ok(bool ok)
+{
+    if (!ok) atomicAdd(&g_iqa_violations, 1u);
+    return ok;
+}
+#define IQA_CHECK(cond) iqa_check_ok(cond)
+// Host reader of this translation unit's counter (read and cleared).
+#define IQA_VIOLATION_READER(name)                                                   \
+    extern "C" unsigned int name()                                                   \
+    {                                                                                \
+        unsigned int v = 0, z = 0;                                                   \
+        cudaMemcpyFromSymbol(&v, g_iqa_violations, sizeof v);                        \
+        cudaMemcpyToSymbol(g_iqa_violations, &z, sizeof z);                          \
+        return v;                                                                    \
+    }
+#else
+#define IQA_CHECK(cond) (true)
+#define IQA_VIOLATION_READER(name)
+#endif
+
 #include <type_traits>
 
 namespace iqa {

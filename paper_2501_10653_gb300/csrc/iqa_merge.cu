@@ -39,15 +39,18 @@ struct MergeArgs {
 
 __device__ __forceinline__ void add4(double (&s)[4], const double *p)
 {
+    if (!p) return;
 #pragma unroll
     for (int k = 0; k < 4; ++k) s[k] += p[k];
 }
 
-// Tile i (row-major) of merged tile b.
+// Tile i (row-major) of merged tile b (nullptr, in the checked build, for an
+// index outside the tile grid).
 __device__ __forceinline__ const double *tile_of(const MergeArgs &a, long long b, long long i)
 {
     const long long R = b / a.M, Cc = b - R * a.M;
     const long long r = R * a.m + i / a.m, c = Cc * a.m + i % a.m;
+    if (!IQA_CHECK(r < a.T && c < a.T && b < (long long)a.M * a.M)) return nullptr;
     return a.sums + 4 * (r * a.T + c);
 }
 
@@ -140,6 +143,8 @@ __global__ void __launch_bounds__(kMergeThreads) iqa_merge_cluster_kernel(MergeA
 }
 
 }  // namespace iqa
+
+IQA_VIOLATION_READER(iqa_read_violations_merge)
 
 using namespace iqa;
 

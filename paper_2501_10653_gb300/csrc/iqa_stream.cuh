@@ -328,6 +328,18 @@ __global__ void __launch_bounds__(CT + 32, 1)
                     mbar_arrive(&full[s]);
                     break;
                 }
+                // the chunk's box lies inside the image and fits one stage
+                // (checked build only; a violation stops the CTA like an abort)
+                if (!IQA_CHECK(pi < npairs && u - d.unit_begin < (long long)d.T * d.units_x &&
+                               col0 >= 0 && col0 + d.TX * d.NT <= d.N &&
+                               (col0 * (int)sizeof(T)) % 16 == 0 &&
+                               (d.NB == 1 || col0 % 256 == 0) &&
+                               row0 + (c + 1) * d.CH <= d.N &&
+                               bytes <= (uint32_t)SB)) {
+                    atomicExch(abort_flag, 1);
+                    ok = false;
+                    break;
+                }
                 stage_unit[s] = u;
                 stage_pair[s] = pi;
                 mbar_expect_tx(&full[s], 2 * bytes);
@@ -400,6 +412,8 @@ __global__ void __launch_bounds__(CT + 32, 1)
             kx = Kahan();
             ky = Kahan();
         }
+        // the chunk's vectors fit the stage (checked build only)
+        if (!IQA_CHECK(V * 16 <= SB)) V = 0;
         const uint4 *xs = reinterpret_cast<const uint4 *>(ring + (size_t)s * 2 * SB);
         const uint4 *ys = reinterpret_cast<const uint4 *>(ring + (size_t)s * 2 * SB + SB);
         Sums2 p;
@@ -452,7 +466,8 @@ __global__ void __launch_bounds__(CT + 32, 1)
             const int trow = (int)(lu / d->units_x);
             const int ucol = (int)(lu - (long long)trow * d->units_x);
             const long long t0 = (long long)trow * d->T + (long long)ucol * TX;
-            for (int tl = tid; tl < TX; tl += CT)
+            const bool out_ok = IQA_CHECK(t0 + TX <= (long long)d->T * d->T && TX <= kMaxTX);
+            for (int tl = tid; tl < TX && out_ok; tl += CT)
                 write_tile_desc(*d, t0 + tl, part[tl * 4 + 0], part[tl * 4 + 1],
                                 part[tl * 4 + 2], part[tl * 4 + 3]);
         }

@@ -11,3 +11,5 @@ cudaError_t launch_stream_bf16(const StreamParams &sp, int ct, int maps, int gri
 }
 
 }  // namespace iqa
+
+IQA_VIOLATION_READER(iqa_read_violations_stream_bf16)

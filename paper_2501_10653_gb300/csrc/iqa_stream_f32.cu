@@ -11,3 +11,5 @@ cudaError_t launch_stream_f32(const StreamParams &sp, int ct, int maps, int grid
 }
 
 }  // namespace iqa
+
+IQA_VIOLATION_READER(iqa_read_violations_stream_f32)

@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "iqa_device.cuh"
 #include "iqa_synth.h"
 
 namespace iqa {
@@ -201,7 +202,9 @@ __global__ void __launch_bounds__(kSynthThreads)
                                 __fadd_rn(sky[1], __fmul_rn(sigma, z.y)),
                                 __fadd_rn(sky[2], __fmul_rn(sigma, z.z)),
                                 __fadd_rn(sky[3], __fmul_rn(sigma, z.w))};
-            store4<T>(out + pix, v);
+            // the four pixels lie in the job's image (checked build only)
+            if (IQA_CHECK(r < j.N && c + 3 < j.N && pix + 3 < (unsigned long long)j.N * j.N))
+                store4<T>(out + pix, v);
         }
         __syncthreads();  // s_* are reused by the next bin
     }
@@ -220,3 +223,5 @@ cudaError_t launch_synth(int dtype, const SynthJob *jobs, const long long *heade
 }
 
 }  // namespace iqa
+
+IQA_VIOLATION_READER(iqa_read_violations_synth)

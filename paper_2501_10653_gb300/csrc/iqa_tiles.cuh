@@ -38,14 +38,18 @@ __global__ void __launch_bounds__(THREADS)
     const T *xu = static_cast<const T *>(p.x) + row0 * p.N + col0;
     const T *yu = static_cast<const T *>(p.y) + row0 * p.N + col0;
 
-    float acc[4];
-    accumulate_unit<T, VEC, ILP, THREADS, DO_A, DO_B>(xu, yu, p.N, p.RH, p.LPU,
-                                                      p.C1f, acc);
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    // the unit lies inside the image (checked build only)
+    if (IQA_CHECK(tile_row < p.T && row0 + p.RH <= p.N &&
+                  col0 + (long long)p.TX * p.NT <= p.N && p.LPU * VEC == p.TX * p.NT))
+        accumulate_unit<T, VEC, ILP, THREADS, DO_A, DO_B>(xu, yu, p.N, p.RH, p.LPU,
+                                                          p.C1f, acc);
     reduce_unit<THREADS>(acc, p.TX, p.LPU, p.LPT, red, part, CtaBarrier());
 
     const long long t0 = (long long)tile_row * p.T + tile_col0;
+    const bool out_ok = IQA_CHECK(t0 + p.TX <= (long long)p.T * p.T && p.TX <= kMaxTX);
     if (p.S == 1) {
-        for (int tl = threadIdx.x; tl < p.TX; tl += THREADS)
+        for (int tl = threadIdx.x; tl < p.TX && out_ok; tl += THREADS)
             write_tile(p, t0 + tl, part[tl * 4 + 0], part[tl * 4 + 1],
                        part[tl * 4 + 2], part[tl * 4 + 3]);
         return;
@@ -53,7 +57,7 @@ __global__ void __launch_bounds__(THREADS)
     // S > 1: the CTAs of this tile form one cluster; combine in rank order.
     cg::cluster_group cluster = cg::this_cluster();
     cluster.sync();
-    if (cluster.block_rank() == 0) {
+    if (cluster.block_rank() == 0 && out_ok) {
         for (int tl = threadIdx.x; tl < p.TX; tl += THREADS) {
             float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
             for (int r = 0; r < p.S; ++r) {

@@ -10,3 +10,5 @@ cudaError_t launch_tiles_f16(const TileArgs &p, const TileConfig &c, int maps,
 }
 
 }  // namespace iqa
+
+IQA_VIOLATION_READER(iqa_read_violations_tiles_f16)

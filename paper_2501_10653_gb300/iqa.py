@@ -14,7 +14,9 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libiqa.so")
+# IQA_LIBRARY selects another build of the same ABI (the tests use it for the
+# bounds-checked libiqa_checked.so); the default is the product library.
+LIB_PATH = os.environ.get("IQA_LIBRARY") or os.path.join(_HERE, "libiqa.so")
 
 IQA_OK = 0
 IQA_PENDING = 1
@@ -153,6 +155,7 @@ def _declare(lib):
         "iqa_get_config": ([_vp, _i, _i, _i, _i, P(iqa_launch_config)], _st),
         "iqa_set_config": ([_vp, _i, _i, _i, _i, P(iqa_launch_config)], _st),
         "iqa_wait": ([_vp, _vp, _i], _st),
+        "iqa_debug_violations": ([P(ctypes.c_ulonglong)], _st),
         "iqa_set_option": ([_vp, _i, ctypes.c_longlong], _st),
         "iqa_plan_create": ([_vp, P(iqa_pair), _i, _i, P(iqa_params), _i, P(_vp)], _st),
         "iqa_plan_launch": ([_vp, _vp], _st),
@@ -301,6 +304,13 @@ def iqa_set_config(ctx, dtype, N, NT, maps, cfg):
             cfg = iqa_launch_config(**full)
         ref = ctypes.byref(cfg)
     return _check(ctx, lib().iqa_set_config(ctx, dtype, N, NT, maps, ref))
+
+
+def iqa_debug_violations():
+    """Failed bounds checks since the last call (checked build only)."""
+    n = ctypes.c_ulonglong(0)
+    _check(None, lib().iqa_debug_violations(ctypes.byref(n)))
+    return n.value
 
 
 def iqa_wait(ctx, stream=None, timeout_us=-1):
