@@ -53,8 +53,8 @@ PROFILED_TRAFFIC = {
     "sources": ["paper_2501_10653_gb300/csrc/iqa_device.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream_f32.cu"],
-    "sha256": "998b8d9e548593b748c7eda947a53d4d4520103e7999db9f6366b18f7de680f2",
-    "bytes_per_pair": (268508160 + 4065280) / 8,
+    "sha256": "9bb578f45e99ff0a52ebd4d7265aa24dad570ecc5fe0aa5f9f2a7f95211a0a66",
+    "bytes_per_pair": (268509952 + 3982592) / 8,
     "capture": "8 pairs per launch, scaled by pairs to the timed launch",
 }
 PAPER_H100 = {"lisi_kernel_ms": 0.101, "auglisi_kernel_ms": 0.091,
