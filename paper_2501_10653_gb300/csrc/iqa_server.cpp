@@ -224,11 +224,10 @@ StreamParams slot_stream_params(const iqa_server *srv, const Slot &s)
 }
 
 // The slot's graphs: work-table uploads, the epoch generator and the
-// persistent map kernel, all sized from device-side headers; graph g runs the
-// kernels on (g+1)/8, 2/8, 4/8 or all of the full persistent grid.
+// persistent map kernel, all sized from device-side headers; graph g = 0..3
+// runs the kernels on 1/8, 1/4, 1/2 or all of the full persistent grid.
 cudaError_t capture_slot(iqa_server *srv, Slot &s)
 {
-    const int M = srv->cfg.max_pairs_per_step;
     const int full = srv->ctx->num_sms * srv->kcfg.ctas_per_sm;
     const int div[4] = {8, 4, 2, 1};
     for (int g = 0; g < 4; ++g) {
