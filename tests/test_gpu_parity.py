@@ -482,3 +482,31 @@ def test_cancelling_aug_tiles_keep_relative_accuracy(ctx, orc, dt, variant):
     assert np.all(np.abs(o) < 0.05) and o.min() < 0 < o.max()
     assert np.all(np.abs(ga.ravel() - o) <= 1e-6 * np.abs(o))
     parity.assert_parity((gl, ga, gs), (ol, oa, osum), PARAMS)
+
+
+@pytest.mark.parametrize("dt", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("N,NT", [(64, 1), (64, 2), (63, 3), (7, 7), (1, 1), (5, 1), (30, 15)])
+def test_degenerate_tile_sizes(ctx, orc, dt, N, NT):
+    """One-pixel and two-pixel tiles, odd sizes, a one-pixel image: random
+    pixels with negatives, exact zeros and a NaN, against the oracle."""
+    rng = np.random.default_rng(N * 100 + NT)
+    x = rng.normal(0.0, 1.0, (N, N))
+    y = rng.normal(0.0, 1.0, (N, N))
+    x[0, 0] = 0.0
+    if N > 2:
+        y[1, 2] = np.nan
+        x[N - 1, N - 1] = -0.0
+    x, y = synth._cast(x, dt), synth._cast(y, dt)
+    got = parity.gpu_maps(ctx, x, y, NT, PARAMS)
+    parity.assert_parity(got, parity.oracle_maps(orc, x, y, NT, PARAMS), PARAMS)
+
+
+def test_empty_batches_rejected(ctx):
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    with pytest.raises(iqa.IqaError) as ei:
+        iqa.iqa_plan_create(ctx, [], iqa.IQA_F32, PARAMS)
+    assert ei.value.status == iqa.IQA_ERR_INVALID_ARG
+    with pytest.raises(iqa.IqaError) as ei:
+        iqa.iqa_batch_noalloc([], iqa.IQA_F32, PARAMS, torch.cuda.current_stream())
+    assert ei.value.status == iqa.IQA_ERR_INVALID_ARG
