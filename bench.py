@@ -288,50 +288,24 @@ def _time_plan(iqa, ctx, plan, stream, K, warmup):
 
 
 def precision_report(iqa, ctx, params, stream, batch=16):
-    """The precision workload (N=8192, N_T=64, point + extended sources, 1e4
-    dynamic range, sigma 5e-3): per-tile error of the FP32 / FP16 / BF16 storage
-    maps against the FP64 oracle on the FP32 originals (storage + accumulation)
-    and on the rounded inputs (accumulation only), and the batched throughput
-    of each storage type."""
+    """The precision workload's size (N=8192, N_T=64, point + extended sources,
+    1e4 dynamic range, sigma 5e-3) stored as FP32, FP16 and BF16: the batched
+    throughput of each storage type.  (The per-tile error of each against the
+    FP64 oracle is measured and bounded by tests/test_gpu_precision.py; the
+    bench runs the oracle only as its CPU baseline.)"""
     import torch
-    import oracle
     from paper_2501_10653_gb300 import synth
     N, NT = 8192, 64
     T = N // NT
-    orc = oracle.Oracle()
-    thr = (os.cpu_count() or 1) if orc.has_openmp else 1
     x32, y32 = synth.precision_pair(0)
-    ol, oa, osum = orc.maps(x32, y32, NT, PARAMS["C1"], PARAMS["C2"], PARAMS["C"],
-                            PARAMS["D"], threads=thr)
-    r32 = osum[:, 1] / (osum[:, 2] + osum[:, 3] + PARAMS["C"])
     out = {"workload": "N=8192 N_T=64, 33 sources (half extended, sigma 5-40 px), peak "
-                       "flux 1e-4..1, noise sigma 5e-3, 10% of sources dropped"}
+                       "flux 1e-4..1, noise sigma 5e-3, 10%% of sources dropped; %d copies of "
+                       "the pair per launch" % batch}
     dev = torch.device("cuda", torch.cuda.current_device())
-
-    def widen(a):
-        return (a.astype(np.uint32) << 16).view(np.float32) if a.dtype == np.uint16 \
-            else a.astype(np.float32)
-
-    for name, code, dt in (("f32", iqa.IQA_F32, "f32"), ("f16", iqa.IQA_F16, "f16"),
-                           ("bf16", iqa.IQA_BF16, "bf16")):
-        x, y = synth._cast(x32.astype(np.float64), dt), synth._cast(y32.astype(np.float64), dt)
+    for name, code in (("f32", iqa.IQA_F32), ("f16", iqa.IQA_F16), ("bf16", iqa.IQA_BF16)):
+        x, y = synth._cast(x32.astype(np.float64), name), synth._cast(y32.astype(np.float64), name)
         tx = torch.from_numpy(x.view(np.int16) if x.dtype == np.uint16 else x).to(dev)
         ty = torch.from_numpy(y.view(np.int16) if y.dtype == np.uint16 else y).to(dev)
-        lm = torch.empty(T * T, device=dev)
-        am = torch.empty(T * T, device=dev)
-        iqa.iqa_both(ctx, tx, ty, code, N, NT, params, lm, am, None, stream)
-        torch.cuda.synchronize()
-        gl = lm.cpu().numpy().astype(np.float64)
-        ga = am.cpu().numpy().astype(np.float64)
-        rl, ra, rsum = orc.maps(widen(x), widen(y), NT, PARAMS["C1"], PARAMS["C2"],
-                                PARAMS["C"], PARAMS["D"], threads=thr)
-        rr = rsum[:, 1] / (rsum[:, 2] + rsum[:, 3] + PARAMS["C"])
-        nz = ol.ravel() > 0
-        st_l = np.abs(gl - ol.ravel())[nz] / ol.ravel()[nz]
-        st_a = np.abs(ga - oa.ravel()) / np.maximum(np.abs(oa.ravel()), r32)
-        ac_l = np.abs(gl - rl.ravel())[rl.ravel() > 0] / rl.ravel()[rl.ravel() > 0]
-        ac_a = np.abs(ga - ra.ravel()) / np.maximum(np.abs(ra.ravel()), rr)
-        # batched throughput: `batch` distinct device pairs of this storage type
         B = batch
         xs = [tx] + [tx.clone() for _ in range(B - 1)]
         ys = [ty] + [ty.clone() for _ in range(B - 1)]
@@ -343,11 +317,6 @@ def precision_report(iqa, ctx, params, stream, batch=16):
         iqa.iqa_plan_destroy(plan)
         es = 4 if name == "f32" else 2
         out[name] = {
-            "storage_error_vs_fp32_originals": {
-                "lisi_rel_max": float(st_l.max()), "lisi_rel_median": float(np.median(st_l)),
-                "aug_max": float(st_a.max()), "aug_median": float(np.median(st_a))},
-            "accumulation_error_vs_rounded_inputs": {
-                "lisi_rel_max": float(ac_l.max()), "aug_max": float(ac_a.max())},
             "batched_GBs": round(20 * B * 2 * N * N * es / (ms * 1e-3) / 1e9, 1),
             "pixel_pairs_per_s": round(20 * B * N * N / (ms * 1e-3), 1),
         }
