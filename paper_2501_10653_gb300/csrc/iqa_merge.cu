@@ -68,6 +68,15 @@ __device__ __forceinline__ void write_merged(const MergeArgs &a, long long b, co
     }
 }
 
+// Programmatic dependent launch: the next kernel in the stream may be
+// scheduled as this grid drains, and this one waits for the previous grid
+// (which wrote the per-tile sums) before its first read.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ __forceinline__ double warp_sum_d(double v)
 {
 #pragma unroll
@@ -78,6 +87,7 @@ __device__ __forceinline__ double warp_sum_d(double v)
 // m^2 <= kThreadMaxTiles: thread b sums its block's tiles row by row.
 __global__ void __launch_bounds__(kMergeThreads) iqa_merge_thread_kernel(MergeArgs a)
 {
+    pdl_enter();
     const long long b = (long long)blockIdx.x * kMergeThreads + threadIdx.x;
     if (b >= (long long)a.M * a.M) return;
     double s[4] = {0.0, 0.0, 0.0, 0.0};
@@ -90,6 +100,7 @@ __global__ void __launch_bounds__(kMergeThreads) iqa_merge_thread_kernel(MergeAr
 // xor-shuffle tree.
 __global__ void __launch_bounds__(kMergeThreads) iqa_merge_warp_kernel(MergeArgs a)
 {
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const long long b = ((long long)blockIdx.x * kMergeThreads + threadIdx.x) >> 5;
     if (b >= (long long)a.M * a.M) return;  // whole warps leave together
@@ -109,6 +120,7 @@ __global__ void __launch_bounds__(kMergeThreads) iqa_merge_cluster_kernel(MergeA
 {
     __shared__ double red[4][kMergeThreads / 32];
     __shared__ double part[4];
+    pdl_enter();
     cg::cluster_group cluster = cg::this_cluster();
     const int q = (int)cluster.block_rank();
     const long long b = blockIdx.x / kClusterCtas;
@@ -172,28 +184,34 @@ extern "C" iqa_status iqa_merge(iqa_ctx *ctx, const double *sums, int T, int m,
     if (s != IQA_OK) return s;
     MergeArgs a{sums, T, m, (int)M, P.C2, P.C, P.D, merged_lisi, merged_aug, merged_sums};
     cudaStream_t st = (cudaStream_t)stream;
+    // every shape launches with programmatic stream serialization (see
+    // pdl_enter); the cluster shape adds its cluster dimension
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.blockDim = dim3(kMergeThreads);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
     if (n <= kThreadMaxTiles) {
-        const long long blocks = (M * M + kMergeThreads - 1) / kMergeThreads;
-        iqa_merge_thread_kernel<<<(unsigned)blocks, kMergeThreads, 0, st>>>(a);
+        cfg.gridDim = dim3((unsigned)((M * M + kMergeThreads - 1) / kMergeThreads));
+        e = cudaLaunchKernelEx(&cfg, iqa_merge_thread_kernel, a);
     } else if (n <= kWarpMaxTiles) {
-        const long long blocks = (M * M * 32 + kMergeThreads - 1) / kMergeThreads;
-        iqa_merge_warp_kernel<<<(unsigned)blocks, kMergeThreads, 0, st>>>(a);
+        cfg.gridDim = dim3((unsigned)((M * M * 32 + kMergeThreads - 1) / kMergeThreads));
+        e = cudaLaunchKernelEx(&cfg, iqa_merge_warp_kernel, a);
     } else {
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[1];
         cfg.gridDim = dim3((unsigned)(M * M * kClusterCtas));
-        cfg.blockDim = dim3(kMergeThreads);
-        cfg.stream = st;
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = kClusterCtas;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        cudaError_t e = cudaLaunchKernelEx(&cfg, iqa_merge_cluster_kernel, a);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "merge kernel launch");
+        attr[1].id = cudaLaunchAttributeClusterDimension;
+        attr[1].val.clusterDim.x = kClusterCtas;
+        attr[1].val.clusterDim.y = 1;
+        attr[1].val.clusterDim.z = 1;
+        cfg.numAttrs = 2;
+        e = cudaLaunchKernelEx(&cfg, iqa_merge_cluster_kernel, a);
     }
-    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "merge kernel launch");
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "merge kernel launch");
     return IQA_OK;
 }
