@@ -452,6 +452,10 @@ typedef struct {
     double input_gb_per_s;     /* algorithmic input bytes of completed pairs / s */
     double mean_pairs_per_step;
     unsigned long long pool_bytes, pool_peak_bytes;
+    /* medians over completed requests of the latency's parts: submission ->
+     * the start of its step's launch calls (queueing), the launch calls
+     * themselves (host), and the rest (device work, read-back, detection) */
+    double p50_queue_ms, p50_launch_ms, p50_device_ms;
 } iqa_server_stats;
 
 /* Creates a server on ctx's device (ctx may be NULL with simulate = 1) and

@@ -118,7 +118,8 @@ struct Request {
     ReqState state = REQ_PENDING;
     iqa_status status = IQA_PENDING;
     bool discard = false;  // drop the maps (and the record) when finished
-    Clock::time_point t_submit, t_done;
+    // submission, the start and the end of its step's launch calls, completion
+    Clock::time_point t_submit, t_launch, t_launched, t_done;
     std::vector<float> lisi, aug;
 };
 
@@ -141,8 +142,15 @@ struct Slot {
     PairDesc *d_pairs = nullptr, *h_pairs = nullptr;
     long long *d_dyn = nullptr, *h_dyn = nullptr;
     unsigned long long *d_sched = nullptr;
-    int *d_status = nullptr, *h_status = nullptr;
-    float *d_out = nullptr, *h_out = nullptr;
+    // the persistent kernel's error word: page-locked and mapped, so the
+    // device writes it (only on a failed wait) and the host reads and clears
+    // it with no copies on the step's stream
+    int *d_status = nullptr;
+    volatile int *h_status = nullptr;
+    // the step's maps: h_out is page-locked and mapped (m_out is its device
+    // address); a step with few tiles has its kernel write the maps there
+    // directly, a larger one writes d_out and copies it back
+    float *d_out = nullptr, *h_out = nullptr, *m_out = nullptr;
     size_t out_cap = 0;
     // one graph per grid size: a step launches the smallest persistent grid
     // that covers its units, so small steps leave SMs to concurrent steps
@@ -180,6 +188,9 @@ struct iqa_server {
     // statistics
     long long submitted = 0, completed = 0, failed = 0, steps = 0, step_pairs = 0;
     std::vector<double> latencies;
+    // per completed request: submission -> launch, the launch calls, and the
+    // rest (device work, read-back and completion detection)
+    std::vector<double> lat_queue, lat_launch, lat_device;
     double bytes_done = 0.0;
     bool have_first = false;
     Clock::time_point t_first, t_last;
@@ -189,6 +200,10 @@ struct iqa_server {
 namespace {
 
 const size_t kMaxQueue = 1 << 20;
+// A step whose maps hold at most this many floats (256 KB) has its kernel
+// write them straight to mapped host memory, which saves the read-back copy
+// (one operation on the step's stream, a few microseconds of latency).
+const size_t kDirectMapFloats = 65536;
 
 void free_slot(Slot &s)
 {
@@ -198,10 +213,9 @@ void free_slot(Slot &s)
     }
     cudaFree(s.d_tab);
     cudaFree(s.d_sched);
-    cudaFree(s.d_status);
     cudaFree(s.d_out);
     cudaFreeHost(s.h_tab);
-    cudaFreeHost(s.h_status);
+    cudaFreeHost(const_cast<int *>(s.h_status));
     cudaFreeHost(s.h_out);
     if (s.ev) cudaEventDestroy(s.ev);
     if (s.st) cudaStreamDestroy(s.st);
@@ -265,10 +279,16 @@ cudaError_t alloc_slot(iqa_server *srv, Slot &s)
     if (e == cudaSuccess) e = cudaMalloc(&s.d_tab, s.tab_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&s.d_sched, 256);
     if (e == cudaSuccess) e = cudaMemset(s.d_sched, 0, 256);
-    if (e == cudaSuccess) e = cudaMalloc(&s.d_status, 256);
-    if (e == cudaSuccess) e = cudaMemset(s.d_status, 0, 256);
     if (e == cudaSuccess) e = cudaMallocHost(&s.h_tab, s.tab_bytes);
-    if (e == cudaSuccess) e = cudaMallocHost(&s.h_status, 256);
+    if (e == cudaSuccess) {
+        int *hs = nullptr;
+        e = cudaHostAlloc(&hs, 256, cudaHostAllocMapped);
+        if (e == cudaSuccess) {
+            std::memset(hs, 0, 256);
+            s.h_status = hs;
+            e = cudaHostGetDevicePointer(&s.d_status, hs, 0);
+        }
+    }
     if (e == cudaSuccess) {
         std::memset(s.h_tab, 0, s.tab_bytes);
         e = cudaMemset(s.d_tab, 0, s.tab_bytes);
@@ -305,9 +325,11 @@ cudaError_t ensure_out(Slot &s, size_t floats)
     cudaFreeHost(s.h_out);
     s.d_out = nullptr;
     s.h_out = nullptr;
+    s.m_out = nullptr;
     s.out_cap = 0;
     cudaError_t e = cudaMalloc(&s.d_out, cap * sizeof(float));
-    if (e == cudaSuccess) e = cudaMallocHost(&s.h_out, cap * sizeof(float));
+    if (e == cudaSuccess) e = cudaHostAlloc(&s.h_out, cap * sizeof(float), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&s.m_out, s.h_out, 0);
     if (e == cudaSuccess) s.out_cap = cap;
     return e;
 }
@@ -331,6 +353,11 @@ iqa_status launch_step(iqa_server *srv, Slot &s)
 
     cudaError_t e = ensure_out(s, floats);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "step output buffers");
+    // the slot's previous step has finished: clear its error word
+    *s.h_status = 0;
+    // maps straight to host memory when they are few (no read-back copy)
+    const bool direct = !srv->cfg.one_pair_per_launch && floats <= kDirectMapFloats;
+    float *out = direct ? s.m_out : s.d_out;
     char *pool = static_cast<char *>(srv->d_pool);
     long long blocks = 0, units = 0;
     size_t o = 0;
@@ -353,7 +380,7 @@ iqa_status launch_step(iqa_server *srv, Slot &s)
         j.add_y = r.r.add_y;
         j.add_flux = r.r.add_flux;
         blocks += (long long)(r.N / kSynthBin) * (r.N / kSynthBin);
-        float *dl = s.d_out + o, *da = s.d_out + o + (size_t)r.T * r.T;
+        float *dl = out + o, *da = out + o + (size_t)r.T * r.T;
         o += 2 * (size_t)r.T * r.T;
         if (srv->cfg.one_pair_per_launch) continue;
         TileConfig c = srv->kcfg;
@@ -397,12 +424,9 @@ iqa_status launch_step(iqa_server *srv, Slot &s)
         while (g < 3 && s.grid[g] < units) ++g;
         e = cudaGraphLaunch(s.exec[g], s.st);
     }
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !direct)
         e = cudaMemcpyAsync(s.h_out, s.d_out, floats * sizeof(float), cudaMemcpyDeviceToHost,
                             s.st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s.h_status, s.d_status, sizeof(int), cudaMemcpyDeviceToHost, s.st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s.d_status, 0, sizeof(int), s.st);
     if (e == cudaSuccess) e = cudaEventRecord(s.ev, s.st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
     return IQA_OK;
@@ -436,6 +460,9 @@ void finish_request(iqa_server *srv, Request &r, iqa_status st, Clock::time_poin
     if (st == IQA_OK) {
         ++srv->completed;
         srv->latencies.push_back(ms_between(r.t_submit, now));
+        srv->lat_queue.push_back(ms_between(r.t_submit, r.t_launch));
+        srv->lat_launch.push_back(ms_between(r.t_launch, r.t_launched));
+        srv->lat_device.push_back(ms_between(r.t_launched, now));
         srv->bytes_done += 2.0 * r.N * r.N * srv->es;
         srv->t_last = now;
     } else {
@@ -569,6 +596,11 @@ void worker_main(iqa_server *srv)
                 // the slot's requests are the worker's alone until retired
                 lk.unlock();
                 const iqa_status st = launch_step(srv, s);
+                const auto t_launched = Clock::now();
+                for (auto &r : s.reqs) {
+                    r->t_launch = s.t_launch;
+                    r->t_launched = t_launched;
+                }
                 lk.lock();
                 if (st != IQA_OK) {
                     // nothing was enqueued that will complete: fail and release now
@@ -1085,6 +1117,13 @@ iqa_status iqa_server_get_stats(iqa_server *srv, iqa_server_stats *out)
         double sum = 0.0;
         for (double x : v) sum += x;
         out->mean_ms = sum / v.size();
+        auto median = [](std::vector<double> w) {
+            std::sort(w.begin(), w.end());
+            return w.empty() ? 0.0 : w[(w.size() - 1) / 2];
+        };
+        out->p50_queue_ms = median(srv->lat_queue);
+        out->p50_launch_ms = median(srv->lat_launch);
+        out->p50_device_ms = median(srv->lat_device);
         const double span_s = ms_between(srv->t_first, srv->t_last) / 1e3;
         if (span_s > 0) {
             out->pairs_per_s = srv->completed / span_s;

@@ -111,7 +111,9 @@ class iqa_server_stats(ctypes.Structure):
                 ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
                 ("pairs_per_s", ctypes.c_double), ("input_gb_per_s", ctypes.c_double),
                 ("mean_pairs_per_step", ctypes.c_double),
-                ("pool_bytes", ctypes.c_ulonglong), ("pool_peak_bytes", ctypes.c_ulonglong)]
+                ("pool_bytes", ctypes.c_ulonglong), ("pool_peak_bytes", ctypes.c_ulonglong),
+                ("p50_queue_ms", ctypes.c_double), ("p50_launch_ms", ctypes.c_double),
+                ("p50_device_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
