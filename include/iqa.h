@@ -399,7 +399,7 @@ typedef unsigned long long iqa_handle;
  * pixel at offset (dy, dx) from its centre.  All arrays are host memory and
  * are copied. */
 typedef struct {
-    int N;                  /* image side, a multiple of 64 */
+    int N;                  /* image side, a multiple of 64, at most 2^20 */
     int nsrc;
     const int *x;           /* source centres, columns */
     const int *y;           /* source centres, rows */

@@ -771,10 +771,11 @@ iqa_status upload_reference(iqa_server *srv, Reference &ref, const iqa_catalog *
 
 iqa_status check_catalog(iqa_ctx *ctx, const iqa_catalog *c)
 {
-    if (!c || c->N < kSynthBin || c->N % kSynthBin || c->nsrc < 0 || c->nprofile < 0 ||
+    if (!c || c->N < kSynthBin || c->N % kSynthBin || c->N > (1 << 20) || c->nsrc < 0 ||
+        c->nprofile < 0 ||
         (c->nsrc > 0 && (!c->x || !c->y || !c->flux || !c->half || !c->profile_off ||
                          !c->profile))) {
-        set_error(ctx, "bad catalogue (N a multiple of 64, arrays for nsrc sources)");
+        set_error(ctx, "bad catalogue (N a multiple of 64 up to 2^20, arrays for nsrc sources)");
         return IQA_ERR_INVALID_ARG;
     }
     for (int i = 0; i < c->nsrc; ++i) {

@@ -38,17 +38,26 @@ constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
 constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+// M independent counters under one key, rounds interleaved: the key schedule
+// is shared and the M multiply chains overlap.  Each round multiplies the
+// counter's words 0 and 2 by the round constants (one 32 x 32 -> 64-bit
+// product each), swaps and XORs the high halves with the other two words and
+// the round key, then bumps the key by the Weyl constants.
+template <int M>
+__device__ __forceinline__ void philox4x32_10(uint4 (&c)[M], uint2 k)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = kPhiloxM0 * c.x, hi0 = __umulhi(kPhiloxM0, c.x);
-        const uint32_t lo1 = kPhiloxM1 * c.z, hi1 = __umulhi(kPhiloxM1, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const unsigned long long p0 = (unsigned long long)kPhiloxM0 * c[i].x;
+            const unsigned long long p1 = (unsigned long long)kPhiloxM1 * c[i].z;
+            c[i] = make_uint4((uint32_t)(p1 >> 32) ^ c[i].y ^ k.x, (uint32_t)p1,
+                              (uint32_t)(p0 >> 32) ^ c[i].w ^ k.y, (uint32_t)p0);
+        }
         k.x += kPhiloxW0;
         k.y += kPhiloxW1;
     }
-    return c;
 }
 
 // Irwin-Hall sum of the four bytes of one Philox word, standardised:
@@ -56,21 +65,44 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
 // two paired 16-bit adds; the integer is exact in float.
 constexpr float kNoiseScale = 1.7320508075688772f / 256.0f;  // exact: a power-of-2 step
 
-__device__ __forceinline__ float irwin_hall4_bytes(uint32_t w)
+// Byte sums, two words at a time: per word, bytes 0/2 and 1/3 are picked into
+// 16-bit lanes and added (each lane <= 510); the two words' lanes are then
+// regrouped so that one add leaves word 0's byte sum s0 in the low half and
+// word 1's s1 in the high half (each <= 1020, no carry).  s - 510 is then
+// formed exactly in float without a conversion instruction: the bits
+// 0x4B000000 + s are the float 2^23 + s, and subtracting 2^23 + 510 is exact.
+__device__ __forceinline__ uint32_t byte_lane_sums(uint32_t w)
 {
-    const uint32_t t = (w & 0x00FF00FFu) + ((w >> 8) & 0x00FF00FFu);
-    const int s = (int)((t & 0xFFFFu) + (t >> 16));
-    return __fmul_rn((float)(s - 510), kNoiseScale);
+    return __byte_perm(w, 0u, 0x4240u) + __byte_perm(w, 0u, 0x4341u);
 }
 
-// Standardised noise of the four horizontally adjacent pixels 4q .. 4q+3 (q
-// = pixel index / 4): one Philox call, word k for pixel 4q + k.
-__device__ __forceinline__ float4 noise_quad(unsigned long long q, unsigned long long seed)
+__device__ __forceinline__ float2 irwin_hall4_bytes2(uint32_t w0, uint32_t w1)
 {
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), 0x5EEDu, 0u),
-                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-    return make_float4(irwin_hall4_bytes(w.x), irwin_hall4_bytes(w.y), irwin_hall4_bytes(w.z),
-                       irwin_hall4_bytes(w.w));
+    const uint32_t t0 = byte_lane_sums(w0), t1 = byte_lane_sums(w1);
+    const uint32_t u = __byte_perm(t0, t1, 0x5410u) + __byte_perm(t0, t1, 0x7632u);
+    const float s0 = __uint_as_float(__byte_perm(u, 0x4B000000u, 0x7610u));
+    const float s1 = __uint_as_float(__byte_perm(u, 0x4B000000u, 0x7632u));
+    return make_float2(__fmul_rn(__fsub_rn(s0, 8389118.0f), kNoiseScale),   // 2^23 + 510
+                       __fmul_rn(__fsub_rn(s1, 8389118.0f), kNoiseScale));
+}
+
+// Standardised noise of M quads of horizontally adjacent pixels 4q .. 4q+3
+// (q = pixel index / 4): one Philox call per quad, word k for pixel 4q + k.
+template <int M>
+__device__ __forceinline__ void noise_quads(const unsigned long long (&q)[M],
+                                            unsigned long long seed, float4 (&z)[M])
+{
+    uint4 w[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+        w[i] = make_uint4((uint32_t)q[i], (uint32_t)(q[i] >> 32), 0x5EEDu, 0u);
+    philox4x32_10<M>(w, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        const float2 a = irwin_hall4_bytes2(w[i].x, w[i].y);
+        const float2 b = irwin_hall4_bytes2(w[i].z, w[i].w);
+        z[i] = make_float4(a.x, a.y, b.x, b.y);
+    }
 }
 
 // Four consecutive pixels rounded to nearest into the storage type and
@@ -138,7 +170,7 @@ __device__ __forceinline__ void add_source(float (&sky)[4], const float *g0, int
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kSynthThreads)
+__global__ void __launch_bounds__(kSynthThreads, 4)
     iqa_synth_kernel(const SynthJob *__restrict__ jobs, const long long *__restrict__ header)
 {
     __shared__ long long s_begin[kSynthMaxJobs];
@@ -159,12 +191,37 @@ __global__ void __launch_bounds__(kSynthThreads)
             if (s_begin[mid] <= b) lo = mid;
             else hi = mid - 1;
         }
+        // the job's and catalogue's fields in registers (the image stores
+        // below could otherwise alias them and force reloads)
         const SynthJob &j = jobs[lo];
         const SynthCatalog &cat = *j.cat;
-        const long long lb = b - s_begin[lo];
+        const int N = j.N;
+        const unsigned long long seed = j.seed;
+        T *const out = static_cast<T *>(j.out);
+        const float *const prof = cat.profile;
+        const float sigma = cat.noise_sigma;
+        // bin within the job (catalogues have N <= 2^20, so fewer than 2^28
+        // bins: a 32-bit division, not the much longer 64-bit routine)
+        const int lb = (int)(b - s_begin[lo]);
         const int bpr = cat.bins_per_row;
-        const int br = (int)(lb / bpr), bc = (int)(lb % bpr);
+        const int br = lb / bpr, bc = lb - br * bpr;
         const int bin = br * bpr + bc;
+        const int r0 = br * kSynthBin, c0 = bc * kSynthBin;
+        // the transient, when its window meets this bin
+        const int tsrc = j.add_src;
+        const float *tg = prof;
+        int th = -1, tx = 0, ty = 0;
+        float tf = 0.0f;
+        if (tsrc >= 0) {
+            th = cat.half[tsrc];
+            tg = prof + cat.profile_off[tsrc];
+            tx = j.add_x;
+            ty = j.add_y;
+            tf = j.add_flux;
+            if (ty + th < r0 || ty - th >= r0 + kSynthBin || tx + th < c0 ||
+                tx - th >= c0 + kSynthBin)
+                th = -1;
+        }
         // stage the bin's non-dropped sources (catalogue order kept)
         if (threadIdx.x == 0) {
             const int q0 = cat.bin_start[bin], q1 = cat.bin_start[bin + 1];
@@ -181,29 +238,33 @@ __global__ void __launch_bounds__(kSynthThreads)
             }
             s_n = n;
         }
+        // the noise of the thread's quads in this bin, all at once (it does
+        // not depend on the sources, so it overlaps their staging)
+        const int c = c0 + lc;
+        constexpr int kQuads = kSynthBin / kRowStep;
+        unsigned long long q[kQuads];
+#pragma unroll
+        for (int k = 0; k < kQuads; ++k)
+            q[k] = ((unsigned long long)(r0 + lr0 + k * kRowStep) * N + c) >> 2;
+        float4 zq[kQuads];
+        noise_quads<kQuads>(q, seed, zq);
         __syncthreads();
-        const int c = bc * kSynthBin + lc;
         const int n = s_n;
-        const float sigma = cat.noise_sigma;
-        T *out = static_cast<T *>(j.out);
-        for (int k = 0; k < kSynthBin / kRowStep; ++k) {
-            const int r = br * kSynthBin + lr0 + k * kRowStep;
-            const unsigned long long pix = (unsigned long long)r * j.N + c;
-            const float4 z = noise_quad(pix >> 2, j.seed);
+#pragma unroll
+        for (int k = 0; k < kQuads; ++k) {
+            const int r = r0 + lr0 + k * kRowStep;
+            const unsigned long long pix = (unsigned long long)r * N + c;
+            const float4 z = zq[k];
             float sky[4] = {0.0f, 0.0f, 0.0f, 0.0f};
             for (int m = 0; m < n; ++m)
-                add_source(sky, cat.profile + s_off[m], s_h[m], r - s_y[m], c - s_x[m], s_f[m]);
-            if (j.add_src >= 0) {
-                const int i = j.add_src;
-                add_source(sky, cat.profile + cat.profile_off[i], cat.half[i], r - j.add_y,
-                           c - j.add_x, j.add_flux);
-            }
+                add_source(sky, prof + s_off[m], s_h[m], r - s_y[m], c - s_x[m], s_f[m]);
+            if (th >= 0) add_source(sky, tg, th, r - ty, c - tx, tf);
             const float v[4] = {__fadd_rn(sky[0], __fmul_rn(sigma, z.x)),
                                 __fadd_rn(sky[1], __fmul_rn(sigma, z.y)),
                                 __fadd_rn(sky[2], __fmul_rn(sigma, z.z)),
                                 __fadd_rn(sky[3], __fmul_rn(sigma, z.w))};
             // the four pixels lie in the job's image (checked build only)
-            if (IQA_CHECK(r < j.N && c + 3 < j.N && pix + 3 < (unsigned long long)j.N * j.N))
+            if (IQA_CHECK(r < N && c + 3 < N && pix + 3 < (unsigned long long)N * N))
                 store4<T>(out + pix, v);
         }
         __syncthreads();  // s_* are reused by the next bin

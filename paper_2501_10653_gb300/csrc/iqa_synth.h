@@ -42,7 +42,8 @@ struct SynthJob {
 
 // Renders every job of the table (at most 64); header = {njobs, total_bins}
 // in device memory (so a captured graph can replay it with new contents).
-// N must be a multiple of kSynthBin, and a bin may list at most 64 sources.
+// N must be a multiple of kSynthBin (at most 2^20), and a bin may list at most
+// 64 sources.
 cudaError_t launch_synth(int dtype, const SynthJob *jobs, const long long *header, int grid,
                          cudaStream_t st);
 
