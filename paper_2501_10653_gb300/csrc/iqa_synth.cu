@@ -61,29 +61,19 @@ __device__ __forceinline__ void philox4x32_10(uint4 (&c)[M], uint2 k)
 }
 
 // Irwin-Hall sum of the four bytes of one Philox word, standardised:
-// z = (b0 + b1 + b2 + b3 - 510) * sqrt(3) / 256.  The byte sum is formed with
-// two paired 16-bit adds; the integer is exact in float.
+// z = (b0 + b1 + b2 + b3 - 510) * sqrt(3) / 256; the integer is exact in
+// float, so the final multiply is the only rounding.
 constexpr float kNoiseScale = 1.7320508075688772f / 256.0f;  // exact: a power-of-2 step
 
-// Byte sums, two words at a time: per word, bytes 0/2 and 1/3 are picked into
-// 16-bit lanes and added (each lane <= 510); the two words' lanes are then
-// regrouped so that one add leaves word 0's byte sum s0 in the low half and
-// word 1's s1 in the high half (each <= 1020, no carry).  s - 510 is then
-// formed exactly in float without a conversion instruction: the bits
-// 0x4B000000 + s are the float 2^23 + s, and subtracting 2^23 + 510 is exact.
-__device__ __forceinline__ uint32_t byte_lane_sums(uint32_t w)
+// The byte sum s of a word is one four-way byte dot product with (1,1,1,1),
+// accumulated onto 0x4B000000: the bits of the float 2^23 + s (s < 2^23),
+// so s - 510 comes out exactly in float by subtracting 2^23 + 510, with no
+// conversion instruction and no integer-pipe work (the generator is bound
+// by the integer pipe, which the Philox rounds already load).
+__device__ __forceinline__ float irwin_hall4_bytes(uint32_t w)
 {
-    return __byte_perm(w, 0u, 0x4240u) + __byte_perm(w, 0u, 0x4341u);
-}
-
-__device__ __forceinline__ float2 irwin_hall4_bytes2(uint32_t w0, uint32_t w1)
-{
-    const uint32_t t0 = byte_lane_sums(w0), t1 = byte_lane_sums(w1);
-    const uint32_t u = __byte_perm(t0, t1, 0x5410u) + __byte_perm(t0, t1, 0x7632u);
-    const float s0 = __uint_as_float(__byte_perm(u, 0x4B000000u, 0x7610u));
-    const float s1 = __uint_as_float(__byte_perm(u, 0x4B000000u, 0x7632u));
-    return make_float2(__fmul_rn(__fsub_rn(s0, 8389118.0f), kNoiseScale),   // 2^23 + 510
-                       __fmul_rn(__fsub_rn(s1, 8389118.0f), kNoiseScale));
+    const uint32_t biased = __dp4a(w, 0x01010101u, 0x4B000000u);
+    return __fmul_rn(__fsub_rn(__uint_as_float(biased), 8389118.0f), kNoiseScale);  // 2^23 + 510
 }
 
 // Standardised noise of M quads of horizontally adjacent pixels 4q .. 4q+3
@@ -98,11 +88,9 @@ __device__ __forceinline__ void noise_quads(const unsigned long long (&q)[M],
         w[i] = make_uint4((uint32_t)q[i], (uint32_t)(q[i] >> 32), 0x5EEDu, 0u);
     philox4x32_10<M>(w, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
 #pragma unroll
-    for (int i = 0; i < M; ++i) {
-        const float2 a = irwin_hall4_bytes2(w[i].x, w[i].y);
-        const float2 b = irwin_hall4_bytes2(w[i].z, w[i].w);
-        z[i] = make_float4(a.x, a.y, b.x, b.y);
-    }
+    for (int i = 0; i < M; ++i)
+        z[i] = make_float4(irwin_hall4_bytes(w[i].x), irwin_hall4_bytes(w[i].y),
+                           irwin_hall4_bytes(w[i].z), irwin_hall4_bytes(w[i].w));
 }
 
 // Four consecutive pixels rounded to nearest into the storage type and
