@@ -132,12 +132,14 @@ __device__ __forceinline__ bool is_dropped(const SynthJob &j, int src)
 
 // Work unit: one catalogue bin (kSynthBin x kSynthBin pixels) of one job per
 // block iteration; thread t takes the four columns 4 (t % 16) .. 4 (t % 16) + 3
-// of rows t / 16 + 16k, k < 4 (one Philox call and one vector store per
-// four pixels), so each warp writes two 64-pixel row segments per step.  The
-// jobs' first-bin offsets live in shared memory (looked up once per bin), and
-// so do the bin's sources (in catalogue order, the order every pixel adds them
-// in).
-constexpr int kSynthThreads = 256;
+// of rows t / 16 + 8k, k < 8 (one Philox call and one vector store per four
+// pixels, in two batches of four rows), so each warp writes two 64-pixel row
+// segments per step and a bin's fixed cost (job and catalogue fields, bin
+// index, source staging, barriers) is paid once per 32 pixels of a thread.
+// The jobs' first-bin offsets live in shared memory (looked up once per bin),
+// and so do the bin's sources (in catalogue order, the order every pixel adds
+// them in).
+constexpr int kSynthThreads = 128;
 constexpr int kSynthMaxJobs = 64;
 constexpr int kSynthBinSrc = 64;  // bin sources staged in shared memory
 constexpr int kQuadsPerRow = kSynthBin / 4;
@@ -158,7 +160,7 @@ __device__ __forceinline__ void add_source(float (&sky)[4], const float *g0, int
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kSynthThreads, 4)
+__global__ void __launch_bounds__(kSynthThreads, kSynthBlocksPerSM)
     iqa_synth_kernel(const SynthJob *__restrict__ jobs, const long long *__restrict__ header)
 {
     __shared__ long long s_begin[kSynthMaxJobs];
@@ -226,34 +228,42 @@ __global__ void __launch_bounds__(kSynthThreads, 4)
             }
             s_n = n;
         }
-        // the noise of the thread's quads in this bin, all at once (it does
-        // not depend on the sources, so it overlaps their staging)
+        // the noise of the thread's first batch of quads (it does not depend on
+        // the sources, so it overlaps their staging)
         const int c = c0 + lc;
-        constexpr int kQuads = kSynthBin / kRowStep;
-        unsigned long long q[kQuads];
+        constexpr int kQuads = kSynthBin / kRowStep;  // rows of a thread in a bin
+        constexpr int kBatch = 4;                     // Philox calls interleaved
+        float4 zq[kBatch];
+        const auto batch_noise = [&](int k0) {
+            unsigned long long q[kBatch];
 #pragma unroll
-        for (int k = 0; k < kQuads; ++k)
-            q[k] = ((unsigned long long)(r0 + lr0 + k * kRowStep) * N + c) >> 2;
-        float4 zq[kQuads];
-        noise_quads<kQuads>(q, seed, zq);
+            for (int k = 0; k < kBatch; ++k)
+                q[k] = ((unsigned long long)(r0 + lr0 + (k0 + k) * kRowStep) * N + c) >> 2;
+            noise_quads<kBatch>(q, seed, zq);
+        };
+        batch_noise(0);
         __syncthreads();
         const int n = s_n;
 #pragma unroll
-        for (int k = 0; k < kQuads; ++k) {
-            const int r = r0 + lr0 + k * kRowStep;
-            const unsigned long long pix = (unsigned long long)r * N + c;
-            const float4 z = zq[k];
-            float sky[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            for (int m = 0; m < n; ++m)
-                add_source(sky, prof + s_off[m], s_h[m], r - s_y[m], c - s_x[m], s_f[m]);
-            if (th >= 0) add_source(sky, tg, th, r - ty, c - tx, tf);
-            const float v[4] = {__fadd_rn(sky[0], __fmul_rn(sigma, z.x)),
-                                __fadd_rn(sky[1], __fmul_rn(sigma, z.y)),
-                                __fadd_rn(sky[2], __fmul_rn(sigma, z.z)),
-                                __fadd_rn(sky[3], __fmul_rn(sigma, z.w))};
-            // the four pixels lie in the job's image (checked build only)
-            if (IQA_CHECK(r < N && c + 3 < N && pix + 3 < (unsigned long long)N * N))
-                store4<T>(out + pix, v);
+        for (int k0 = 0; k0 < kQuads; k0 += kBatch) {
+            if (k0 > 0) batch_noise(k0);
+#pragma unroll
+            for (int k = 0; k < kBatch; ++k) {
+                const int r = r0 + lr0 + (k0 + k) * kRowStep;
+                const unsigned long long pix = (unsigned long long)r * N + c;
+                const float4 z = zq[k];
+                float sky[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                for (int m = 0; m < n; ++m)
+                    add_source(sky, prof + s_off[m], s_h[m], r - s_y[m], c - s_x[m], s_f[m]);
+                if (th >= 0) add_source(sky, tg, th, r - ty, c - tx, tf);
+                const float v[4] = {__fadd_rn(sky[0], __fmul_rn(sigma, z.x)),
+                                    __fadd_rn(sky[1], __fmul_rn(sigma, z.y)),
+                                    __fadd_rn(sky[2], __fmul_rn(sigma, z.z)),
+                                    __fadd_rn(sky[3], __fmul_rn(sigma, z.w))};
+                // the four pixels lie in the job's image (checked build only)
+                if (IQA_CHECK(r < N && c + 3 < N && pix + 3 < (unsigned long long)N * N))
+                    store4<T>(out + pix, v);
+            }
         }
         __syncthreads();  // s_* are reused by the next bin
     }

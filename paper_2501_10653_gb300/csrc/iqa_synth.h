@@ -40,6 +40,10 @@ struct SynthJob {
     float add_flux;              // transient peak flux
 };
 
+// Resident generator blocks per SM; a grid of num_sms * kSynthBlocksPerSM
+// keeps every SM full (the kernel loops over the bins).
+constexpr int kSynthBlocksPerSM = 8;
+
 // Renders every job of the table (at most 64); header = {njobs, total_bins}
 // in device memory (so a captured graph can replay it with new contents).
 // N must be a multiple of kSynthBin (at most 2^20), and a bin may list at most
