@@ -244,7 +244,9 @@ __global__ void __launch_bounds__(kSynthThreads, kSynthBlocksPerSM)
         batch_noise(0);
         __syncthreads();
         const int n = s_n;
-#pragma unroll
+        // the batches are not unrolled: one copy of the row body keeps the
+        // kernel within the instruction cache
+#pragma unroll 1
         for (int k0 = 0; k0 < kQuads; k0 += kBatch) {
             if (k0 > 0) batch_noise(k0);
 #pragma unroll
