@@ -622,13 +622,16 @@ def run_ours(args):
         hy16 = [t.to(tdt) for t in dy]
         pairs16 = [iqa.make_pair(hx16[i], hy16[i], N, NT, lisi[i], aug[i]) for i in range(B)]
         pl16 = iqa.iqa_plan_create(ctx, pairs16, code, params, 0)
+        tuned16 = (iqa.iqa_plan_autotune(pl16, stream, args.tune_iters).as_dict()
+                   if args.tune_iters > 0 else None)
         K16 = max(10, min(K, 2000))
         ms = _time_plan(iqa, ctx, pl16, stream, K16, 3)
         iqa.iqa_plan_destroy(pl16)
         storage16[name] = {
             "GBs": round(K16 * B * pair_bytes / 2 / (ms * 1e-3) / 1e9, 1),
             "pixel_pairs_per_s": round(K16 * B * N * N / (ms * 1e-3), 1),
-            "us_per_pair": round(ms * 1e3 / (K16 * B), 3)}
+            "us_per_pair": round(ms * 1e3 / (K16 * B), 3),
+            "tuned": tuned16}
         del hx16, hy16
 
     prec = None
