@@ -56,7 +56,7 @@ typedef enum {
     IQA_ERR_CUDA = -3,         /* a CUDA call failed (text in last_error)     */
     IQA_ERR_TIMEOUT = -4,      /* a bounded wait ran out                      */
     IQA_ERR_BUSY = -5,         /* queue or slot table full                    */
-    IQA_ERR_UNSUPPORTED = -6   /* valid request this build cannot serve       */
+    IQA_ERR_UNSUPPORTED = -6   /* valid request the compiled library lacks    */
 } iqa_status;
 
 /* Pixel storage type of both input images. */

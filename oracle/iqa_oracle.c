@@ -139,7 +139,7 @@ int iqa_oracle_maps(const float *x, const float *y, long N, long NT,
     return 0;
 }
 
-/* 1 when this build spreads tiles over OpenMP threads, else 0. */
+/* 1 when compiled with OpenMP (tiles spread over threads), else 0. */
 int iqa_oracle_has_openmp(void)
 {
 #ifdef _OPENMP
