@@ -510,3 +510,49 @@ def test_empty_batches_rejected(ctx):
     with pytest.raises(iqa.IqaError) as ei:
         iqa.iqa_batch_noalloc([], iqa.IQA_F32, PARAMS, torch.cuda.current_stream())
     assert ei.value.status == iqa.IQA_ERR_INVALID_ARG
+
+
+def _near_equal_pair(dt):
+    """A 5 x 5-tile image whose tile column c holds pixel pairs that differ by
+    delta_c = 0, one storage ulp, C1/2, C1 and 1000 C1 (each y rounded to the
+    storage type, so the smallest steps may round back to zero): the LISI
+    denominator |x' - y'| + C1 from exactly C1 upward."""
+    NT, n = 32, 5
+    N = NT * n
+    rng = np.random.default_rng(11)
+    x = synth._cast(rng.uniform(1e-3, 1.0, (N, N)), dt)
+    xs = parity.widen(x).astype(np.float64)
+    col = np.arange(N) // NT
+    C1 = PARAMS["C1"]
+    y = synth._cast(xs + np.array([0.0, 0.0, 0.5 * C1, C1, 1e3 * C1])[col][None, :], dt)
+    ulp = col == 1
+    if dt == "bf16":
+        y[:, ulp] = x[:, ulp] + np.uint16(1)  # next bf16 up (positive values)
+    else:
+        y[:, ulp] = np.nextafter(x[:, ulp], np.array(np.inf, x.dtype))
+    return x, y, NT
+
+
+@pytest.mark.parametrize("dt", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_lisi_near_zero_denominator(ctx, orc, dt, variant):
+    """LISI's per-pixel denominator |x' - y'| + C1 adds two nonnegative
+    numbers, so FP32 keeps its relative error at one rounding however small
+    |x' - y'| is (|x' - y'| itself is exact for x', y' within a factor 2):
+    tiles of equal, one-ulp-apart and C1-apart pixels match the oracle to the
+    FP32 tolerance with no FP64 in the per-pixel path."""
+    from paper_2501_10653_gb300 import iqa
+    x, y, NT = _near_equal_pair(dt)
+    N = x.shape[0]
+    d = np.abs(parity.widen(x).astype(np.float64) - parity.widen(y).astype(np.float64))
+    assert d[:, :NT].max() == 0.0 and d[:, NT:2 * NT].min() > 0.0
+    code = parity.dtype_code(x)
+    cfg = dict(variant=variant, threads=128, tiles_across=1)
+    if variant == 1:
+        cfg.update(stages=4, stage_kb=4)
+    iqa.iqa_set_config(ctx, code, N, NT, iqa.MAPS_BOTH, cfg)
+    try:
+        got = parity.gpu_maps(ctx, x, y, NT, PARAMS)
+    finally:
+        iqa.iqa_set_config(ctx, code, N, NT, iqa.MAPS_BOTH, None)
+    parity.assert_parity(got, parity.oracle_maps(orc, x, y, NT, PARAMS), PARAMS)
