@@ -145,6 +145,18 @@ def paper_pair(pair_index=0, dtype="f32", N=None):
     return sky_pair(pair_index=pair_index, dtype=dtype, **w)
 
 
+def paper_pair_dropped(pair_index=0):
+    """The sources that epoch 2 of ``paper_pair(pair_index)`` leaves out: the
+    same catalogue draw (the sky stream's first draw), its ``n_drop``
+    faintest.  Returns their (x, y, flux) arrays, columns x and rows y in
+    pixels."""
+    w = dict(PAPER_PAIR_N2048)
+    rng_sky = np.random.default_rng([w["seed"], 0, pair_index])
+    cat = catalog(rng_sky, w["N"], w["n_src"], w["flux"][0], w["flux"][1], w["fwhm"])
+    gone = np.argsort(cat["flux"], kind="stable")[:w["n_drop"]]
+    return cat["x"][gone], cat["y"][gone], cat["flux"][gone]
+
+
 def mixed_batch_specs(n_pairs=64, seed=2):
     """The batched workload's draw: N from {1024, 2048, 4096, 8192} with weights
     4:3:2:1 and N_T from {32, 64, 128}, per pair.  Returns a list of (N, NT)."""

@@ -556,3 +556,11 @@ def test_lisi_near_zero_denominator(ctx, orc, dt, variant):
     finally:
         iqa.iqa_set_config(ctx, code, N, NT, iqa.MAPS_BOTH, None)
     parity.assert_parity(got, parity.oracle_maps(orc, x, y, NT, PARAMS), PARAMS)
+
+
+def test_auglisi_localises_dropped_sources(ctx, paper):
+    """The paper-level behaviour on the CUDA maps: the dropped sources' tiles
+    are exactly the lowest augLISI values of the paper-scale pair."""
+    import test_paper_behaviour as pb
+    l, a, _ = parity.gpu_maps(ctx, paper[0], paper[1], pb.NT, PARAMS)
+    pb.check_localisation(l, a)
