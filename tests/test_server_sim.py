@@ -182,3 +182,29 @@ def test_native_trace_driver(lib):
         assert st.completed == 100 and st.pending == 0 and st.p99_ms > 0
     finally:
         iqa.iqa_server_destroy(srv)
+
+
+def test_latency_split_adds_up(lib):
+    """The statistics split each request's latency into queueing, the launch
+    calls and the rest (device work, or here its modelled time); one request
+    at a time, the parts' medians add up to the median latency and the rest
+    matches the modelled step time.  Medians over 30 requests: the first few
+    after set-up can wait for a core while the catalogue set-up's numpy
+    threads wind down."""
+    rate = 2e9  # 2 N^2 * 2 bytes of an N=1024 FP16 pair = 4 MiB -> about 2.1 ms
+    srv = _server(lib, sim_bytes_per_s=rate)
+    try:
+        for i in range(30):
+            h = iqa.iqa_submit(srv, iqa.make_request(1, 64, 300 + i))
+            assert _wait_all(srv, [h])[h] == iqa.IQA_OK
+        st = iqa.iqa_server_get_stats(srv)
+        model_ms = 1e3 * 2 * 1024 * 1024 * 2 / rate
+        assert st.completed == 30
+        assert 0.0 <= st.p50_queue_ms < st.p50_ms and 0.0 <= st.p50_launch_ms < st.p50_ms
+        # the modelled time runs from the start of the launch calls, the
+        # device part from their end (microseconds later)
+        assert model_ms - 0.05 <= st.p50_device_ms < model_ms + 2.0
+        parts = st.p50_queue_ms + st.p50_launch_ms + st.p50_device_ms
+        assert abs(parts - st.p50_ms) < 0.5
+    finally:
+        iqa.iqa_server_destroy(srv)
