@@ -286,6 +286,17 @@ typedef struct iqa_plan iqa_plan;
 /* iqa_plan_create flag: capture the launch as a CUDA graph, replayed by
  * iqa_plan_launch. */
 #define IQA_PLAN_GRAPH 1
+/* iqa_plan_create flag: the caller promises that, whenever the plan is
+ * launched, the kernel just before it on the stream does not write the plan's
+ * images, does not read its maps or sums, and writes them, if at all, only
+ * with the values this launch writes.  The plan's own previous launch
+ * qualifies (a plan's results repeat bit for bit), and so does another
+ * plan's launch over other outputs.  Each CTA then starts copying its first
+ * unit while that kernel drains, instead of after it completes; every other
+ * access, and the launch's completion, still follow it.  Breaking the
+ * promise gives wrong maps, not a fault.  Effective for direct launches (a
+ * graph replay waits for the previous work anyway). */
+#define IQA_PLAN_INDEPENDENT 2
 
 /*
  * Builds a plan over `npairs` pairs: validates them, encodes one TMA tensor

@@ -103,6 +103,7 @@ static StreamParams plan_params(const iqa_plan *pl)
     sp.timeout_ns = pl->ctx->wait_timeout_ns;
     sp.sched = pl->d_sched;
     sp.inject_stall = pl->ctx->inject_stall;
+    sp.overlap_head = (pl->flags & IQA_PLAN_INDEPENDENT) ? 1 : 0;
     return sp;
 }
 
@@ -172,6 +173,10 @@ iqa_status iqa_plan_create(iqa_ctx *ctx, const iqa_pair *pairs, int npairs, iqa_
     *out = nullptr;
     if (!dtype_ok(dtype)) {
         set_error(ctx, "unknown dtype %d", (int)dtype);
+        return IQA_ERR_INVALID_ARG;
+    }
+    if (flags & ~(IQA_PLAN_GRAPH | IQA_PLAN_INDEPENDENT)) {
+        set_error(ctx, "unknown plan flags 0x%x", flags);
         return IQA_ERR_INVALID_ARG;
     }
     iqa_params P;

@@ -70,10 +70,14 @@ struct StreamParams {
     // Dynamic schedule (nullable: static round-robin instead): [0] = next
     // unit, [1] = CTAs done fetching.  Zero before the launch; the last CTA to
     // finish fetching puts both back to zero, so a stream of launches needs no
-    // reset in between (launches sharing a counter must not overlap).
+    // reset in between (launches sharing a counter must not use it at the same
+    // time: even an independent launch waits for the kernel before it first).
     unsigned long long *sched;
     int inject_stall;        // test hook: 1 = the producer issues nothing
-    int pad2_;
+    // 1: the launch does not depend on the kernel before it in the stream
+    // (an independent plan): each CTA's first unit is copied before waiting
+    // for that kernel, and only the shared counter waits for it
+    int overlap_head;
     // nullable: {npairs, total_units} in device memory, read at launch in
     // place of the two fields above (a captured graph replayed with new work)
     const long long *dyn;
@@ -254,9 +258,30 @@ __global__ void __launch_bounds__(CT + 32, 1)
         constexpr uint32_t kGrabBytes = 65536;
         long long u = blockIdx.x, u_end = u + 1, nxt = -1, nxt_end = -1, i = 0;
         bool have_next = false;
-        // a kernel earlier in the stream (programmatic dependent launch) may
-        // still be running: wait for it before any work is fetched or copied
-        asm volatile("griddepcontrol.wait;" ::: "memory");
+        // A kernel earlier in the stream (programmatic dependent launch) may
+        // still be running: wait for it before any work is fetched or copied.
+        // An independent launch (sp.overlap_head) instead issues its first
+        // unit's copies at once, overlapping that kernel's drain, and waits
+        // before it touches the shared counter, which that kernel may still
+        // be using (and so that this grid never completes before it).
+        bool waited = sp.overlap_head == 0;
+        if (waited) asm volatile("griddepcontrol.wait;" ::: "memory");
+        // next grab of units (one atomicAdd on the shared counter, or the
+        // static round-robin without one), sized from the current unit
+        const auto fetch_next = [&](uint32_t unit_bytes) {
+            if (sp.sched) {
+                unsigned g = unit_bytes >= kGrabBytes ? 1u : min(8u, kGrabBytes / unit_bytes);
+                const long long share = (total_units - u) / (4LL * gridDim.x);
+                if (share < (long long)g) g = (unsigned)(share > 1 ? share : 1);
+                nxt = (long long)gridDim.x +
+                      (long long)atomicAdd(&sp.sched[0], (unsigned long long)g);
+                nxt_end = nxt + g;
+            } else {
+                nxt = blockIdx.x + (++i) * (long long)gridDim.x;
+                nxt_end = nxt + 1;
+            }
+            have_next = true;
+        };
         if (sp.inject_stall) ok = false;  // test hook: issue nothing at all
         // pair of unit u: units are taken in increasing order, so the pair
         // index only moves forward (a binary search only when u passes the
@@ -294,22 +319,7 @@ __global__ void __launch_bounds__(CT + 32, 1)
                 col0 = (int)(lu - (long long)trow * d.units_x) * d.TX * d.NT;
                 row0 = trow * d.NT;
                 bytes = (uint32_t)(d.CH * d.TX * d.NT * (int)sizeof(T));
-                if (!have_next) {
-                    if (sp.sched) {
-                        const uint32_t unit_bytes = bytes * (uint32_t)d.chunks;
-                        unsigned g =
-                            unit_bytes >= kGrabBytes ? 1u : min(8u, kGrabBytes / unit_bytes);
-                        const long long share = (total_units - u) / (4LL * gridDim.x);
-                        if (share < (long long)g) g = (unsigned)(share > 1 ? share : 1);
-                        nxt = (long long)gridDim.x +
-                              (long long)atomicAdd(&sp.sched[0], (unsigned long long)g);
-                        nxt_end = nxt + g;
-                    } else {
-                        nxt = blockIdx.x + (++i) * (long long)gridDim.x;
-                        nxt_end = nxt + 1;
-                    }
-                    have_next = true;
-                }
+                if (!have_next && waited) fetch_next(bytes * (uint32_t)d.chunks);
             }
             for (int c = 0; c < nchunks; ++c, ++k) {
                 const int s = (int)(k % S);
@@ -352,6 +362,12 @@ __global__ void __launch_bounds__(CT + 32, 1)
                     tma_load_2d(dst + SB, &d.tmy, col0, row0 + c * d.CH, &full[s]);
                 }
             }
+            if (!waited) {
+                // the first unit is in flight (independent launch)
+                asm volatile("griddepcontrol.wait;" ::: "memory");
+                waited = true;
+                if (!last && ok) fetch_next(bytes * (uint32_t)d.chunks);
+            }
             if (last) break;
             if (++u >= u_end) {
                 u = nxt;
@@ -359,6 +375,7 @@ __global__ void __launch_bounds__(CT + 32, 1)
                 have_next = false;
             }
         }
+        if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
         if (sp.sched) {
             // every CTA has made its final fetch once the count reaches the
             // grid size; the last one puts the counters back to zero (the

@@ -131,6 +131,7 @@ class iqa_plan_stats(ctypes.Structure):
 
 
 IQA_PLAN_GRAPH = 1
+IQA_PLAN_INDEPENDENT = 2
 IQA_NOALLOC_MAX_PAIRS = 64
 IQA_OPT_WAIT_TIMEOUT_US = 1
 IQA_OPT_INJECT_STALL = 2

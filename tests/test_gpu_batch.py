@@ -198,3 +198,52 @@ def test_rewritten_descriptor_tables_are_reread(ctx, orc):
                 x, y = b.host[i]
                 parity.assert_parity(b.results(i), parity.oracle_maps(orc, x, y, NT, PARAMS),
                                      PARAMS)
+
+
+def test_independent_plans_back_to_back(ctx, orc):
+    """IQA_PLAN_INDEPENDENT: each CTA copies its first unit while the kernel
+    before it drains, and waits for that kernel before its shared counter.
+    Eight independent plans over the same pairs, each writing its own
+    NaN-filled maps, launched back to back (each launch's head overlaps the
+    previous one's tail), then one plan launched six times back to back:
+    every map fully written and bit-identical to a default plan's, whose
+    maps match the oracle."""
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    specs = _specs()[:8]
+    ref = Batch(specs)
+    _run(ctx, ref, flags=0)
+    want = [ref.results(i) for i in range(len(specs))]
+    for i, (N, NT) in enumerate(specs[:3]):
+        x, y = ref.host[i]
+        parity.assert_parity(want[i], parity.oracle_maps(orc, x, y, NT, PARAMS), PARAMS)
+    outs = [Batch.__new__(Batch) for _ in range(8)]
+    plans = []
+    try:
+        for o in outs:
+            o.specs, o.host, o.dev = ref.specs, ref.host, ref.dev
+            o.out = [tuple(torch.full_like(t, float("nan")) for t in ref.out[i])
+                     for i in range(len(specs))]
+            plans.append(iqa.iqa_plan_create(ctx, o.pairs(), iqa.IQA_F32, PARAMS,
+                                             iqa.IQA_PLAN_INDEPENDENT))
+        st = torch.cuda.current_stream()
+        for p in plans:
+            iqa.iqa_plan_launch(p, st)
+        for _ in range(5):
+            iqa.iqa_plan_launch(plans[0], st)
+        iqa.iqa_wait(ctx, st, 20_000_000)
+    finally:
+        for p in plans:
+            iqa.iqa_plan_destroy(p)
+    for o in outs:
+        for i in range(len(specs)):
+            for u, v in zip(o.results(i), want[i]):
+                assert np.array_equal(u, v)
+
+
+def test_plan_rejects_unknown_flags(ctx):
+    from paper_2501_10653_gb300 import iqa
+    b = Batch(_specs()[:1])
+    with pytest.raises(iqa.IqaError) as ei:
+        iqa.iqa_plan_create(ctx, b.pairs(), iqa.IQA_F32, PARAMS, 4)
+    assert ei.value.status == iqa.IQA_ERR_INVALID_ARG

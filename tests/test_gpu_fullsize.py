@@ -38,11 +38,12 @@ def _picks(T, rng, k):
                                      [0, T - 1, T * T - T, T * T - 1]]))
 
 
-def _plan_run(ctx, pairs, code, tune_iters, launches):
+def _plan_run(ctx, pairs, code, tune_iters, launches, flags=None):
     import torch
     from paper_2501_10653_gb300 import iqa
     st = torch.cuda.Stream()
-    plan = iqa.iqa_plan_create(ctx, pairs, code, PARAMS, iqa.IQA_PLAN_GRAPH)
+    flags = iqa.IQA_PLAN_GRAPH if flags is None else flags
+    plan = iqa.iqa_plan_create(ctx, pairs, code, PARAMS, flags)
     try:
         if tune_iters:
             iqa.iqa_plan_autotune(plan, st, tune_iters)
@@ -57,7 +58,9 @@ def _plan_run(ctx, pairs, code, tune_iters, launches):
 
 def test_headline_configuration_every_tile(ctx, orc):
     """bench.py's timed step: 32 distinct paper-scale pairs (the same seeded
-    inputs), one persistent launch, autotuned and replayed back to back."""
+    inputs), one persistent launch of an independent plan, autotuned and
+    launched directly back to back (each launch's head overlapping the
+    previous one's tail)."""
     import torch
     from paper_2501_10653_gb300 import iqa
     N, NT, B = 2048, 64, 32
@@ -67,7 +70,7 @@ def test_headline_configuration_every_tile(ctx, orc):
     outs = [(torch.full((T * T,), float("nan"), device="cuda"),
              torch.full((T * T,), float("nan"), device="cuda")) for _ in range(B)]
     pairs = [iqa.make_pair(d[0], d[1], N, NT, o[0], o[1]) for d, o in zip(dev, outs)]
-    _plan_run(ctx, pairs, iqa.IQA_F32, 2, 5)
+    _plan_run(ctx, pairs, iqa.IQA_F32, 2, 5, iqa.IQA_PLAN_INDEPENDENT)
     for (x, y), (lm, am) in zip(host, outs):
         want = parity.oracle_maps(orc, x, y, NT, PARAMS)
         parity.assert_parity((lm.cpu().numpy(), am.cpu().numpy(), None), want, PARAMS)
