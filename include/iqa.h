@@ -315,8 +315,10 @@ iqa_status iqa_plan_create(iqa_ctx *ctx, const iqa_pair *pairs, int npairs,
 /*
  * Enqueues the plan's launch (graph replay, or a direct launch) on `stream`.
  * Stream-ordered, returns without synchronising.  Launches of the same plan
- * must not overlap in time (they share the plan's work counter): issue them
- * on one stream, or order them with events.
+ * share its work counter, so they must be ordered: issue them on one stream,
+ * or order them with events.  (On one stream, an IQA_PLAN_INDEPENDENT plan's
+ * launch overlaps the previous kernel only in its first units' copies; it
+ * still waits for that kernel before it touches the counter.)
  */
 iqa_status iqa_plan_launch(iqa_plan *plan, iqa_stream stream);
 
