@@ -585,6 +585,25 @@ def run_ours(args):
         p1.record(stream)
     torch.cuda.synchronize()
     per_pair_us = p0.elapsed_time(p1) * 1e3 / (reps * G)
+    # one pair per launch through the plan API instead: B one-pair independent
+    # plans launched directly back to back (each launch's first units stream
+    # while the previous one drains)
+    one_plans = [iqa.iqa_plan_create(ctx, [iqa.make_pair(dx[i], dy[i], N, NT, lisi[i], aug[i])],
+                                     iqa.IQA_F32, params, iqa.IQA_PLAN_INDEPENDENT)
+                 for i in range(B)]
+    with torch.cuda.stream(stream):
+        for i in range(3 * B):
+            iqa.iqa_plan_launch(one_plans[i % B], stream)
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for i in range(reps * G):
+            iqa.iqa_plan_launch(one_plans[i % B], stream)
+        q1.record(stream)
+    torch.cuda.synchronize()
+    plan_pair_us = q0.elapsed_time(q1) * 1e3 / (reps * G)
+    for p in one_plans:
+        iqa.iqa_plan_destroy(p)
     def single_launches(fn, count):
         """Device time of `count` isolated launches (a GPU-side delay queued
         ahead of each, so the launch is already queued when the events run);
@@ -733,6 +752,8 @@ def run_ours(args):
                 "lisi_only_single_us_median10": round(float(np.median(lisi_only)), 3),
                 "auglisi_only_single_us_median10": round(float(np.median(aug_only)), 3),
                 "launch": plain_cfg,
+                "independent_plans_us_per_pair": round(plan_pair_us, 3),
+                "independent_plans_GBs": round(pair_bytes / (plan_pair_us * 1e-6) / 1e9, 1),
                 "timing": "back-to-back iqa_both launches replayed from a CUDA graph; "
                           "single launches (60 of both maps, 10 of each map alone) each "
                           "with a GPU-side delay queued ahead, rotating over the step's "
