@@ -43,6 +43,7 @@ N_IMG = 2048
 N_TILE = 64
 PARAMS = {"C1": 1e-6, "C2": 1e-6, "C": 1e-6, "D": 0.5e-6}
 PAPER_NT_SWEEP = (16, 32, 64, 128, 256)
+PAPER_N_SWEEP = (512, 1024, 2048, 4096, 8192)
 
 # DRAM traffic of the timed kernel from one ncu capture (summary and command in
 # profiles/iqa_stream_kernel_N2048_NT64_batch8_f32.md): dram__bytes_read.sum +
@@ -669,6 +670,50 @@ def run_ours(args):
     prec = None
     if rank == 0 and world == 1 and not args.no_precision:
         prec = precision_report(iqa, ctx, params, stream, args.precision_batch)
+
+    # N sweep at N_T = 64 (the paper's other Fig. 1 axis), about the same bytes
+    # per launch at every N, built on the device from the step's pairs:
+    # N < 2048 as contiguous pieces of each 2048^2 image, N > 2048 as mosaics
+    # of them; independent plans, autotuned like the rest
+    nsweep = {}
+    for n2 in PAPER_N_SWEEP:
+        if n2 == N:
+            continue
+        if n2 < N:
+            k = (N // n2) ** 2
+            xs = [dx[i].reshape(-1)[j * n2 * n2:(j + 1) * n2 * n2]
+                  for i in range(B) for j in range(k)]
+            ys = [dy[i].reshape(-1)[j * n2 * n2:(j + 1) * n2 * n2]
+                  for i in range(B) for j in range(k)]
+        else:
+            r = n2 // N
+
+            def mosaic(imgs, c):
+                t = [imgs[(c * r * r + q) % B].view(N, N) for q in range(r * r)]
+                return torch.cat([torch.cat(t[a * r:(a + 1) * r], dim=1) for a in range(r)],
+                                 dim=0).reshape(-1).contiguous()
+            count = max(1, B // (r * r))
+            xs = [mosaic(dx, c) for c in range(count)]
+            ys = [mosaic(dy, c) for c in range(count)]
+        t2 = n2 // NT
+        outs = [(torch.empty(t2 * t2, device=dev), torch.empty(t2 * t2, device=dev))
+                for _ in xs]
+        pl = iqa.iqa_plan_create(ctx, [iqa.make_pair(xs[i], ys[i], n2, NT, *outs[i])
+                                       for i in range(len(xs))],
+                                 iqa.IQA_F32, params, iqa.IQA_PLAN_INDEPENDENT)
+        if args.tune_iters > 0:
+            iqa.iqa_plan_autotune(pl, stream, args.tune_iters)
+        KS = max(10, min(K, 200))
+        ms = _time_plan(iqa, ctx, pl, stream, KS, 3)
+        iqa.iqa_plan_destroy(pl)
+        nsweep[str(n2)] = {"pairs_per_launch": len(xs),
+                           "us_per_pair": round(ms * 1e3 / (KS * len(xs)), 3),
+                           "GBs": round(KS * len(xs) * 2 * n2 * n2 * 4 / (ms * 1e-3) / 1e9, 1)}
+        del xs, ys, outs
+    nsweep[str(N)] = {"pairs_per_launch": B, "us_per_pair": round(dev_ms * 1e3 / (K * B), 3),
+                      "GBs": round(K * B * pair_bytes / (dev_ms * 1e-3) / 1e9, 1)}
+    torch.cuda.empty_cache()
+
     merge = None
     if rank == 0 and world == 1 and not args.no_merge:
         merge = merge_report(iqa, params, ctx, stream, dx[0], dy[0])
@@ -761,6 +806,7 @@ def run_ours(args):
                           "times are quantised to about 2 us on this GPU, so the mean of 60 "
                           "is the finer figure"},
             "nt_sweep_GBs": sweep,
+            "n_sweep_NT64": nsweep,
             "storage_16bit": storage16,
             "clocks": clk,
             "e2e": {"value": round(e2e_value, 2), "unit": "GB/s",
