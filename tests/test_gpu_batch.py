@@ -200,7 +200,8 @@ def test_rewritten_descriptor_tables_are_reread(ctx, orc):
                                      PARAMS)
 
 
-def test_independent_plans_back_to_back(ctx, orc):
+@pytest.mark.parametrize("dt,code", [("f32", 0), ("f16", 1), ("bf16", 2)])
+def test_independent_plans_back_to_back(ctx, orc, dt, code):
     """IQA_PLAN_INDEPENDENT: each CTA copies its first unit while the kernel
     before it drains, and waits for that kernel before its shared counter.
     Eight independent plans over the same pairs, each writing its own
@@ -211,8 +212,8 @@ def test_independent_plans_back_to_back(ctx, orc):
     import torch
     from paper_2501_10653_gb300 import iqa
     specs = _specs()[:8]
-    ref = Batch(specs)
-    _run(ctx, ref, flags=0)
+    ref = Batch(specs, dtype=dt)
+    _run(ctx, ref, flags=0, dtype_code=code)
     want = [ref.results(i) for i in range(len(specs))]
     for i, (N, NT) in enumerate(specs[:3]):
         x, y = ref.host[i]
@@ -224,7 +225,7 @@ def test_independent_plans_back_to_back(ctx, orc):
             o.specs, o.host, o.dev = ref.specs, ref.host, ref.dev
             o.out = [tuple(torch.full_like(t, float("nan")) for t in ref.out[i])
                      for i in range(len(specs))]
-            plans.append(iqa.iqa_plan_create(ctx, o.pairs(), iqa.IQA_F32, PARAMS,
+            plans.append(iqa.iqa_plan_create(ctx, o.pairs(), code, PARAMS,
                                              iqa.IQA_PLAN_INDEPENDENT))
         st = torch.cuda.current_stream()
         for p in plans:
