@@ -59,7 +59,26 @@ typedef enum {
     IQA_ERR_UNSUPPORTED = -6   /* valid request the compiled library lacks    */
 } iqa_status;
 
-/* Pixel storage type of both input images. */
+/*
+ * Pixel storage type of both input images.  Pixels are widened to float32
+ * exactly and every sum runs in float32 (compensated), so the maps match the
+ * exact Eq. 1 / Eq. 2 values of the STORED pixels to 1e-5 relative in every
+ * type.  Against the float32 originals that were rounded to FP16 / BF16,
+ * each tile also carries the storage error, which is bounded from the
+ * originals alone (per pixel, the rounding moves a clamped value v by at most
+ * e(v) = max(u v, eta), u = 2^-11 / 2^-8, eta = 2^-25 / 2^-134 for FP16 /
+ * BF16, and 0 for v = 0; with s = x + y, d = |x - y|, t = d + C1 and
+ * es = e(x) + e(y)):
+ *   |d lisi| <= D (EA M + A EM) / (M max(C2, M - EM)),
+ *       EA = sum es (t + s) / (t max(C1, t - es)),  M = max(Sx, Sy) + C2,
+ *       EM = max(sum e(x), sum e(y));
+ *   |d aug|  <= (EB Q + B EQ) / (Q max(C, Q - EQ)),
+ *       EB = sum (es d + s es + es^2),  Q = Sx + Sy + C,  EQ = sum es.
+ * The LISI bound is small only where the storage spacing u v stays well
+ * below |x - y| + C1; with C1 = 1e-6 it is of the order of LISI itself for
+ * pixels above about 2e-3 (FP16) or 2.6e-4 (BF16), i.e. LISI of noisy skies
+ * should be computed from FP32 pixels.  augLISI has no such amplification.
+ */
 typedef enum {
     IQA_F32 = 0,
     IQA_F16 = 1,
@@ -70,8 +89,11 @@ typedef enum {
  * Constants of Eq. 1 and Eq. 2.  Section 1 only says C1, C2, C << 1 and never
  * defines D.  Defaults (iqa_default_params): C1 = C2 = C = 1e-6 and D = C1/2,
  * the value for which identical inputs give LISI -> 1 and every LISI lies in
- * [0, 1].  D <= 0 on input means "use C1/2".  Requirements: C1 > 0, C2 >= 0,
- * C >= 0, all finite.
+ * [0, 1].  D <= 0 on input means "use C1/2".  Requirements: C1 at least the
+ * smallest normal float32 (about 1.18e-38; the per-pixel divide of Eq. 1 runs
+ * in float32), C2 >= 0, C >= 0, all finite.  Range: the per-pixel terms and
+ * the tile sums are float32, so (x + y) / C1 summed over a tile must stay
+ * below about 3.4e38 (with C1 = 1e-6, pixels far beyond any sky image).
  */
 typedef struct {
     double C1;
@@ -373,13 +395,16 @@ iqa_status iqa_wait(iqa_ctx *ctx, iqa_stream stream, int timeout_us);
  *
  * Set-up: the first call on each device looks up the array's device address
  * (with that device current); make that first call before any stream capture.
- * Every call copies its descriptors into the array and clears the counters on
- * `stream`, then launches there, and returns without synchronising.  All calls
- * share the one array, which keeps the last call's contents: calls whose work
- * overlaps on the GPU (on different streams, or from different threads) race
- * and give wrong maps, so order them on one stream or with events.  A device-
- * side wait that runs out leaves maps unwritten and is not reported here (the
- * plan path reports it through iqa_wait).
+ * Every call passes its descriptors by value, as the argument of a small
+ * kernel that writes them into the array and clears the counters on `stream`
+ * (no host buffer outlives the call), then launches the map kernel there, and
+ * returns without synchronising.  All calls share the one array, which keeps
+ * the last call's contents: calls whose work overlaps on the GPU (on
+ * different streams, or from different threads) race and give wrong maps, so
+ * order them on one stream or with events.  A device-side wait that runs out
+ * (bounded at 1 s) leaves maps unwritten and is not reported here (the plan
+ * path reports it through iqa_wait); a caller that must detect it fills its
+ * maps with NaN before the call and checks that none is left.
  * Errors: IQA_ERR_INVALID_ARG (more than IQA_NOALLOC_MAX_PAIRS pairs, a bad
  * pair, dtype or constants), IQA_ERR_UNSUPPORTED (a pair the TMA kernel cannot
  * stream, as for iqa_plan_create), IQA_ERR_CUDA.  Reason: iqa_last_error(NULL).

@@ -41,6 +41,36 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 namespace {
 
+// A call's descriptor table, passed by value as the argument of the kernel
+// that writes it into the scratch (kernel arguments may take up to 32764
+// bytes), so that no host buffer has to outlive the call.
+struct NoallocTable {
+    PairDesc descs[IQA_NOALLOC_MAX_PAIRS];
+    int npairs;
+};
+static_assert(sizeof(NoallocTable) <= 32764, "descriptor table exceeds a kernel argument");
+static_assert(sizeof(PairDesc) % 16 == 0, "descriptors are copied in 16-byte words");
+
+// Writes the call's descriptors into the scratch and clears the work counters
+// and the status word.  The map kernel that follows on the stream reads the
+// tensor maps through the tensor-map proxy: release these writes to it.
+__global__ void __launch_bounds__(256) iqa_noalloc_stage_kernel(const __grid_constant__
+                                                                NoallocTable tab)
+{
+    const uint4 *src = reinterpret_cast<const uint4 *>(tab.descs);
+    uint4 *dst = reinterpret_cast<uint4 *>(g_noalloc_scratch);
+    const int words = tab.npairs * (int)(sizeof(PairDesc) / 16);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+    if (threadIdx.x < 16)
+        reinterpret_cast<uint4 *>(g_noalloc_scratch + kCounterOffset)[threadIdx.x] =
+            make_uint4(0u, 0u, 0u, 0u);
+    asm volatile("fence.proxy.tensormap::generic.release.gpu;" ::: "memory");
+}
+
+}  // namespace
+
+namespace {
+
 std::mutex g_setup_mu;
 void *g_scratch_addr[kMaxDevices] = {};
 int g_num_sms[kMaxDevices] = {};
@@ -114,10 +144,13 @@ extern "C" iqa_status iqa_batch_noalloc(const iqa_pair *pairs, int npairs, iqa_d
     s = scratch_for_current_device(&scratch, &num_sms);
     if (s != IQA_OK) return s;
 
-    // Descriptors are built in a fixed-size host array on the stack, largest
-    // tiles first, and copied into the device array on the caller's stream.
-    alignas(alignof(PairDesc)) unsigned char host_buf[kDescBytes];
-    PairDesc *host = reinterpret_cast<PairDesc *>(host_buf);
+    // Descriptors are built in the staging kernel's argument (on the stack),
+    // largest tiles first; that kernel writes them into the device array on
+    // the caller's stream.
+    NoallocTable tab;
+    std::memset(&tab, 0, sizeof tab);
+    tab.npairs = npairs;
+    PairDesc *host = tab.descs;
     int order[IQA_NOALLOC_MAX_PAIRS];
     for (int i = 0; i < npairs; ++i) order[i] = i;
     std::stable_sort(order, order + npairs,
@@ -144,11 +177,11 @@ extern "C" iqa_status iqa_batch_noalloc(const iqa_pair *pairs, int npairs, iqa_d
         if (p.aug_map) maps |= MAPS_B;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    // pageable source: the copy has left host_buf when the call returns
-    cudaError_t e = cudaMemcpyAsync(scratch, host, sizeof(PairDesc) * npairs,
-                                    cudaMemcpyHostToDevice, st);
-    // the work counters and the status word must start at zero
-    if (e == cudaSuccess) e = cudaMemsetAsync(scratch + kCounterOffset, 0, 256, st);
+    // descriptors in, counters and status word to zero: one kernel whose
+    // argument carries the table (launched in full stream order, so a
+    // previous call's map kernel on this stream has finished with the array)
+    iqa_noalloc_stage_kernel<<<1, 256, 0, st>>>(tab);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "scratch set-up");
 
     StreamParams sp;
