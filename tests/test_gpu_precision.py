@@ -5,21 +5,27 @@ every tile against the FP64 oracle (needs a GPU).
 * accumulation error -- the maps against the oracle on the same (rounded)
   pixels: the FP32-accumulation bound of parity.py (1e-5) for every storage
   type;
-* storage error -- the maps against the oracle on the FP32 originals: bounded
-  for augLISI (1e-5 with FP16, 2e-4 with BF16 on this workload); for LISI it is
-  reported, not bounded: its per-pixel 1/(|x - y| + C1) with C1 = 1e-6
-  amplifies the rounding of nearly equal noise pixels without limit.
+* storage + accumulation error -- the maps against the oracle on the FP32
+  originals, asserted on every tile against the stated bound: the storage
+  bound of ``oracle.storage_bound`` (computed from the originals alone, a
+  guarantee for any input) plus the accumulation tolerance:
+      |lisi_gpu - lisi_32| <= Lb + 1e-5 lisi_rounded
+      |aug_gpu  - aug_32 | <= Ab + 1e-5 max(|aug_rounded|, r_rounded)
+  For LISI the storage bound is large on this workload (the per-pixel
+  1/(|x - y| + C1) with C1 = 1e-6 amplifies the rounding of nearly equal noise
+  pixels: FP16 and BF16 spacing at the 5e-3 noise level exceeds C1), and
+  states exactly that; for augLISI it is small.
 Run with -s to see the table."""
 import numpy as np
 import pytest
 
 import parity
+from oracle import storage_bound
 from paper_2501_10653_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
 PARAMS = {"C1": 1e-6, "C2": 1e-6, "C": 1e-6, "D": 0.0}
-AUG_STORAGE_BOUND = {"f32": 1e-6, "f16": 1e-5, "bf16": 2e-4}
 
 
 @pytest.fixture(scope="module")
@@ -45,6 +51,7 @@ def _rel(g, o):
 @pytest.mark.parametrize("dt", ["f32", "f16", "bf16"])
 def test_storage_and_accumulation_error(ctx, orc, originals, dt):
     x32, y32, (ol, oa, osum) = originals
+    ol, oa = ol.ravel(), oa.ravel()
     x = synth._cast(x32.astype(np.float64), dt)
     y = synth._cast(y32.astype(np.float64), dt)
     gl, ga, gs = parity.gpu_maps(ctx, x, y, 64, PARAMS)
@@ -52,19 +59,29 @@ def test_storage_and_accumulation_error(ctx, orc, originals, dt):
     ga = ga.astype(np.float64).ravel()
     # accumulation: against the oracle on the rounded pixels
     rl, ra, rsum = parity.oracle_maps(orc, x, y, 64, PARAMS)
+    rl, ra = rl.ravel(), ra.ravel()
     parity.assert_parity((gl, ga, gs), (rl, ra, rsum), PARAMS)
     rr = rsum[:, 1] / (rsum[:, 2] + rsum[:, 3] + PARAMS["C"])
-    acc_l = _rel(gl, rl.ravel())
-    acc_a = np.abs(ga - ra.ravel()) / np.maximum(np.abs(ra.ravel()), rr)
+    acc_l = _rel(gl, rl)
+    acc_a = np.abs(ga - ra) / np.maximum(np.abs(ra), rr)
     # storage + accumulation: against the oracle on the FP32 originals
     r32 = osum[:, 1] / (osum[:, 2] + osum[:, 3] + PARAMS["C"])
-    st_l = _rel(gl, ol.ravel())
-    st_a = np.abs(ga - oa.ravel()) / np.maximum(np.abs(oa.ravel()), r32)
+    st_l = _rel(gl, ol)
+    st_a = np.abs(ga - oa) / np.maximum(np.abs(oa), r32)
+    lb, ab, bl, ba = storage_bound.tile_bounds(x32, y32, 64, dt, PARAMS["C1"], PARAMS["C2"],
+                                               PARAMS["C"], PARAMS["D"])
+    assert np.allclose(bl, ol, rtol=1e-12)
     print("\n%-4s accumulation: lisi rel max %.2e, aug max %.2e | storage: lisi rel "
-          "median %.2e max %.2e, aug median %.2e max %.2e"
-          % (dt, acc_l.max(), acc_a.max(), np.median(st_l), st_l.max(), np.median(st_a),
-             st_a.max()))
-    assert acc_l.max() <= 1e-5 and acc_a.max() <= 1e-5
-    assert st_a.max() <= AUG_STORAGE_BOUND[dt]
+          "median %.2e max %.2e (bound max %.2e), aug median %.2e max %.2e (bound max %.2e)"
+          % (dt, acc_l.max(), acc_a.max(), np.median(st_l), st_l.max(),
+             np.max(lb / ol), np.median(st_a), st_a.max(),
+             np.max(ab / np.maximum(np.abs(oa), r32))))
+    assert acc_l.max() <= parity.REL and acc_a.max() <= parity.REL
+    tol_l = lb + parity.REL * np.abs(rl)
+    tol_a = ab + parity.REL * np.maximum(np.abs(ra), rr)
+    bad_l = np.abs(gl - ol) > tol_l
+    bad_a = np.abs(ga - oa) > tol_a
+    assert not bad_l.any(), "%s lisi: %d tiles beyond the stated bound" % (dt, bad_l.sum())
+    assert not bad_a.any(), "%s aug: %d tiles beyond the stated bound" % (dt, bad_a.sum())
     if dt == "f32":
-        assert st_l.max() <= 1e-5
+        assert st_l.max() <= parity.REL
