@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <cfloat>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -75,8 +76,11 @@ iqa_status resolve_params(iqa_ctx *ctx, const iqa_params *in, iqa_params *out)
                   p.C1, p.C2, p.C);
         return IQA_ERR_INVALID_ARG;
     }
-    if ((float)p.C1 <= 0.0f) {
-        set_error(ctx, "C1=%g underflows float32", p.C1);
+    // The per-pixel divide of Eq. 1 runs in float32 on d + C1 with a
+    // reciprocal that flushes subnormals: C1 must round to a normal float.
+    if (p.C1 < (double)FLT_MIN || (float)p.C1 < FLT_MIN) {
+        set_error(ctx, "C1=%g is below the smallest normal float32 (%g)", p.C1,
+                  (double)FLT_MIN);
         return IQA_ERR_INVALID_ARG;
     }
     if (p.D <= 0.0) p.D = p.C1 / 2.0;
@@ -133,13 +137,40 @@ bool any_config_valid(int N, int NT, iqa_dtype dtype, const TileConfig &c,
     return false;
 }
 
+// CTAs of the tile kernel in shape c that one SM holds at once (0 if the
+// runtime cannot tell), cached per context.
+static int tiles_occupancy(iqa_ctx *ctx, iqa_dtype dtype, const TileConfig &c, int maps)
+{
+    const auto key = std::make_tuple((int)dtype, c.vec * 1000 + c.ilp, c.threads, maps);
+    {
+        std::lock_guard<std::mutex> g(ctx->cfg_mu);
+        auto it = ctx->occupancy.find(key);
+        if (it != ctx->occupancy.end()) return it->second;
+    }
+    TileArgs none;
+    std::memset(&none, 0, sizeof none);
+    int occ = 0;
+    cudaError_t e = dtype == IQA_F32   ? launch_tiles_f32(none, c, maps, 0, nullptr, &occ)
+                    : dtype == IQA_F16 ? launch_tiles_f16(none, c, maps, 0, nullptr, &occ)
+                                       : launch_tiles_bf16(none, c, maps, 0, nullptr, &occ);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        occ = 0;
+    }
+    std::lock_guard<std::mutex> g(ctx->cfg_mu);
+    ctx->occupancy[key] = occ;
+    return occ;
+}
+
 // Launch shape when nothing was tuned (measured on GB300: 128-thread CTAs
 // with 8 loads of each image in flight per thread, and units of up to 16K
-// pixel pairs, stream best).  Units shrink for small images so that there are
+// pixel pairs, stream best).  Units shrink for large images so that there are
 // at least about six per SM, for load balance, but not below one tile while
-// there are at least as many tiles as SMs (splitting a tile over a cluster
-// only to balance measured slower: 10.9 against 8.9 us for one N=1024,
-// N_T=64 pair); tiles larger than a unit are split over a cluster of CTAs.
+// there are at least as many tiles as SMs.  With fewer tiles than SMs (small
+// images), each tile gets its own CTA (256 threads once it has 1024 vectors
+// per image), and only tiles above 8K pixel pairs (32 KB per image) are split
+// over a cluster of CTAs: a cluster launch costs more than it saves on
+// smaller tiles (N=256, N_T=64: 7.4 against 8.8 us per isolated launch).
 TileConfig default_config(int N, int NT, iqa_dtype dtype, bool aligned,
                           int num_sms)
 {
@@ -151,9 +182,10 @@ TileConfig default_config(int N, int NT, iqa_dtype dtype, bool aligned,
     const long long img_px = (long long)N * N;
     long long target = (es == 4 ? 16384 : 32768);
     const int sms = num_sms > 0 ? num_sms : 152;
+    const bool few_tiles = (long long)T * T < sms;
     const long long balance = img_px / (6LL * sms);
     const long long floor_px =
-        (long long)T * T >= sms ? std::min<long long>(tile_px, target) : 2048;
+        few_tiles ? 32768 / es : std::min<long long>(tile_px, target);
     while (target > floor_px && target > balance) target /= 2;
     c.vec = (aligned && NT % V == 0) ? V : 1;
     c.threads = 128;
@@ -168,7 +200,7 @@ TileConfig default_config(int N, int NT, iqa_dtype dtype, bool aligned,
             }
         c.S = S;
         if (tile_px / S > 4 * target) c.threads = 512;
-    } else {
+    } else if (!few_tiles) {
         int best = 1;
         for (int tx = 2; tx <= kMaxTX && tx <= T; ++tx) {
             if (T % tx) continue;
@@ -178,6 +210,8 @@ TileConfig default_config(int N, int NT, iqa_dtype dtype, bool aligned,
             best = tx;
         }
         c.TX = best;
+    } else if ((long long)NT * LPT >= 1024) {
+        c.threads = 256;
     }
     if (c.vec == 1) {
         c.threads = 256;
@@ -186,6 +220,35 @@ TileConfig default_config(int N, int NT, iqa_dtype dtype, bool aligned,
         long long vecs = (long long)(NT / c.S) * c.TX * LPT;
         long long per_thread = vecs / c.threads;
         c.ilp = per_thread >= 8 ? 8 : per_thread >= 4 ? 4 : 2;
+    }
+    return c;
+}
+
+// One wave: when the units of a one-pair launch need more than one but at
+// most two waves of resident CTAs (the last wave then runs a fraction of the
+// GPU and its ramp and tail are paid twice), units twice as wide that fit one
+// wave are used instead (N=2048, N_T=64: 512 CTAs of two tiles, 12.96 against
+// 14.3 us per isolated launch).
+static TileConfig fit_one_wave(iqa_ctx *ctx, int N, int NT, iqa_dtype dtype, int maps,
+                               TileConfig c)
+{
+    if (c.variant != 0 || c.S != 1 || c.vec == 1) return c;
+    const int T = N / NT;
+    const long long sms = ctx->num_sms > 0 ? ctx->num_sms : 152;
+    const long long units = (long long)(T / c.TX) * T;
+    const int occ = tiles_occupancy(ctx, dtype, c, maps);
+    if (occ <= 0 || units <= occ * sms || units > 2 * occ * sms) return c;
+    const int LPT = NT / c.vec;
+    for (int tx = c.TX + 1; tx <= std::min(T, kMaxTX); ++tx) {
+        if (T % tx || tx % c.TX) continue;
+        const long long lpu = (long long)tx * LPT;
+        if (lpu > c.threads || c.threads % lpu) continue;
+        TileConfig w = c;
+        w.TX = tx;
+        long long per_thread = (long long)NT * lpu / w.threads;
+        w.ilp = per_thread >= 8 ? 8 : per_thread >= 4 ? 4 : 2;
+        const int occ_w = tiles_occupancy(ctx, dtype, w, maps);
+        if (occ_w > 0 && (long long)(T / tx) * T <= occ_w * sms) return w;
     }
     return c;
 }
@@ -201,16 +264,17 @@ TileConfig pick_config(iqa_ctx *ctx, int N, int NT, iqa_dtype dtype, int maps,
             if ((c.variant == 0 && c.vec == 1) || aligned) return c;
         }
     }
-    return default_config(N, NT, dtype, aligned, ctx->num_sms);
+    return fit_one_wave(ctx, N, NT, dtype, maps,
+                        default_config(N, NT, dtype, aligned, ctx->num_sms));
 }
 
 cudaError_t launch_tiles(const TileArgs &p, const TileConfig &c, iqa_dtype dtype,
                          int maps, int rows, cudaStream_t st)
 {
     switch (dtype) {
-    case IQA_F32: return launch_tiles_f32(p, c, maps, rows, st);
-    case IQA_F16: return launch_tiles_f16(p, c, maps, rows, st);
-    default: return launch_tiles_bf16(p, c, maps, rows, st);
+    case IQA_F32: return launch_tiles_f32(p, c, maps, rows, st, nullptr);
+    case IQA_F16: return launch_tiles_f16(p, c, maps, rows, st, nullptr);
+    default: return launch_tiles_bf16(p, c, maps, rows, st, nullptr);
     }
 }
 

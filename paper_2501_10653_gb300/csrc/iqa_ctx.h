@@ -31,6 +31,9 @@ struct iqa_ctx {
     // keyed by (dtype, N, NT, maps)
     std::mutex cfg_mu;
     std::map<std::tuple<int, int, int, int>, iqa::TileConfig> pinned;
+    // resident CTAs per SM of one-pair kernel shapes, keyed by (dtype,
+    // vec * 1000 + ilp, threads, maps)
+    std::map<std::tuple<int, int, int, int>, int> occupancy;
     // batched-kernel shape per dtype, set by iqa_plan_autotune
     iqa::TileConfig batch_cfg[3];
     bool has_batch_cfg[3] = {false, false, false};

@@ -31,14 +31,15 @@ constexpr int kMaxTX = 64;
 constexpr int kMaxCluster = 8;
 
 // Launch the tile kernel for tile rows [p.tile_row0, p.tile_row0 + rows).
-// `maps` says which numerator sums are formed (MapsMask).  Defined once per
-// storage type in iqa_tiles_<type>.cu.
+// `maps` says which numerator sums are formed (MapsMask).  With occ non-null
+// nothing is launched: *occ receives how many CTAs of that kernel fit one SM.
+// Defined once per storage type in iqa_tiles_<type>.cu.
 cudaError_t launch_tiles_f32(const TileArgs &p, const TileConfig &c, int maps,
-                             int rows, cudaStream_t st);
+                             int rows, cudaStream_t st, int *occ);
 cudaError_t launch_tiles_f16(const TileArgs &p, const TileConfig &c, int maps,
-                             int rows, cudaStream_t st);
+                             int rows, cudaStream_t st, int *occ);
 cudaError_t launch_tiles_bf16(const TileArgs &p, const TileConfig &c, int maps,
-                              int rows, cudaStream_t st);
+                              int rows, cudaStream_t st, int *occ);
 
 struct StreamParams;
 cudaError_t launch_stream_f32(const StreamParams &sp, int ct, int maps, int grid,

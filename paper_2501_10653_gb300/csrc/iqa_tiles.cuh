@@ -72,9 +72,14 @@ __global__ void __launch_bounds__(THREADS)
     cluster.sync();
 }
 
+// Launches the kernel, or, with occ non-null, stores the number of its CTAs
+// that fit one SM at once (no launch).
 template <typename T, int VEC, int ILP, int THREADS, bool DO_A, bool DO_B>
-static cudaError_t launch_one(const TileArgs &p, int rows, cudaStream_t st)
+static cudaError_t launch_one(const TileArgs &p, int rows, cudaStream_t st, int *occ)
 {
+    if (occ)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            occ, iqa_tiles_kernel<T, VEC, ILP, THREADS, DO_A, DO_B>, THREADS, 0);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(p.T / p.TX), (unsigned)(rows * p.S), 1);
     cfg.blockDim = dim3(THREADS, 1, 1);
@@ -96,43 +101,43 @@ static cudaError_t launch_one(const TileArgs &p, int rows, cudaStream_t st)
 }
 
 template <typename T, int VEC, int ILP, int THREADS>
-static cudaError_t by_maps(const TileArgs &p, int maps, int rows, cudaStream_t st)
+static cudaError_t by_maps(const TileArgs &p, int maps, int rows, cudaStream_t st, int *occ)
 {
     switch (maps) {
-    case MAPS_A: return launch_one<T, VEC, ILP, THREADS, true, false>(p, rows, st);
-    case MAPS_B: return launch_one<T, VEC, ILP, THREADS, false, true>(p, rows, st);
-    default: return launch_one<T, VEC, ILP, THREADS, true, true>(p, rows, st);
+    case MAPS_A: return launch_one<T, VEC, ILP, THREADS, true, false>(p, rows, st, occ);
+    case MAPS_B: return launch_one<T, VEC, ILP, THREADS, false, true>(p, rows, st, occ);
+    default: return launch_one<T, VEC, ILP, THREADS, true, true>(p, rows, st, occ);
     }
 }
 
 template <typename T, int VEC, int ILP>
 static cudaError_t by_threads(const TileArgs &p, const TileConfig &c, int maps,
-                              int rows, cudaStream_t st)
+                              int rows, cudaStream_t st, int *occ)
 {
     switch (c.threads) {
-    case 128: return by_maps<T, VEC, ILP, 128>(p, maps, rows, st);
-    case 256: return by_maps<T, VEC, ILP, 256>(p, maps, rows, st);
-    case 512: return by_maps<T, VEC, ILP, 512>(p, maps, rows, st);
+    case 128: return by_maps<T, VEC, ILP, 128>(p, maps, rows, st, occ);
+    case 256: return by_maps<T, VEC, ILP, 256>(p, maps, rows, st, occ);
+    case 512: return by_maps<T, VEC, ILP, 512>(p, maps, rows, st, occ);
     default: return cudaErrorInvalidValue;
     }
 }
 
 template <typename T>
 static cudaError_t launch_tiles_t(const TileArgs &p, const TileConfig &c,
-                                  int maps, int rows, cudaStream_t st)
+                                  int maps, int rows, cudaStream_t st, int *occ)
 {
     constexpr int V = Elem<T>::VEC;
     if (c.vec == 1) {
         // scalar path for unaligned images or tiles that are not a whole
         // number of 16-byte vectors wide: one launch shape only
         if (c.threads != 256 || c.ilp != 8) return cudaErrorInvalidValue;
-        return by_maps<T, 1, 8, 256>(p, maps, rows, st);
+        return by_maps<T, 1, 8, 256>(p, maps, rows, st, occ);
     }
     if (c.vec != V) return cudaErrorInvalidValue;
     switch (c.ilp) {
-    case 2: return by_threads<T, V, 2>(p, c, maps, rows, st);
-    case 4: return by_threads<T, V, 4>(p, c, maps, rows, st);
-    case 8: return by_threads<T, V, 8>(p, c, maps, rows, st);
+    case 2: return by_threads<T, V, 2>(p, c, maps, rows, st, occ);
+    case 4: return by_threads<T, V, 4>(p, c, maps, rows, st, occ);
+    case 8: return by_threads<T, V, 8>(p, c, maps, rows, st, occ);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -4,9 +4,9 @@
 namespace iqa {
 
 cudaError_t launch_tiles_f16(const TileArgs &p, const TileConfig &c, int maps,
-                             int rows, cudaStream_t st)
+                             int rows, cudaStream_t st, int *occ)
 {
-    return launch_tiles_t<__half>(p, c, maps, rows, st);
+    return launch_tiles_t<__half>(p, c, maps, rows, st, occ);
 }
 
 }  // namespace iqa

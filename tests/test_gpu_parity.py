@@ -558,6 +558,43 @@ def test_lisi_near_zero_denominator(ctx, orc, dt, variant):
     parity.assert_parity(got, parity.oracle_maps(orc, x, y, NT, PARAMS), PARAMS)
 
 
+FLT_MIN = float(np.finfo(np.float32).tiny)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_smallest_accepted_c1(ctx, orc, variant):
+    """C1 must be at least the smallest normal float32: the per-pixel divide of
+    Eq. 1 runs in float32 with a reciprocal that flushes subnormals.  At
+    exactly that C1 (and D = C1/2, a subnormal float32) the maps match the
+    oracle, with equal pixel pairs whose terms are s / C1; any smaller C1 is
+    rejected before anything is launched."""
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    rng = np.random.default_rng(41)
+    N, NT = 128, 32
+    x = rng.uniform(-2e-16, 1e-15, (N, N)).astype(np.float32)
+    y = rng.uniform(-2e-16, 1e-15, (N, N)).astype(np.float32)
+    y[:, ::3] = x[:, ::3]
+    p = {"C1": FLT_MIN, "C2": FLT_MIN, "C": FLT_MIN, "D": 0.0}
+    cfg = dict(variant=variant, threads=128, tiles_across=1)
+    if variant == 1:
+        cfg.update(stages=4, stage_kb=4)
+    iqa.iqa_set_config(ctx, iqa.IQA_F32, N, NT, iqa.MAPS_BOTH, cfg)
+    try:
+        got = parity.gpu_maps(ctx, x, y, NT, p)
+    finally:
+        iqa.iqa_set_config(ctx, iqa.IQA_F32, N, NT, iqa.MAPS_BOTH, None)
+    parity.assert_parity(got, parity.oracle_maps(orc, x, y, NT, p), p)
+    d = torch.zeros(64 * 64, device="cuda")
+    m = torch.full((16,), float("nan"), device="cuda")
+    for c1 in (float(np.nextafter(np.float32(FLT_MIN), np.float32(0))), FLT_MIN * (1 - 1e-9)):
+        with pytest.raises(iqa.IqaError) as ei:
+            iqa.iqa_both(ctx, d, d, iqa.IQA_F32, 64, 16, dict(p, C1=c1), m, None)
+        assert ei.value.status == iqa.IQA_ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    assert np.all(np.isnan(m.cpu().numpy()))
+
+
 def test_auglisi_localises_dropped_sources(ctx, paper):
     """The paper-level behaviour on the CUDA maps: the dropped sources' tiles
     are exactly the lowest augLISI values of the paper-scale pair."""
