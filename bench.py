@@ -83,7 +83,7 @@ def parse_args(argv=None):
                     help="skip the N=8192 FP32/FP16/BF16 precision and throughput report")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the 64-pair mixed-size batch report")
-    ap.add_argument("--serve-seconds", type=float, default=5.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the served Poisson trace (0: skip serving)")
     ap.add_argument("--precision-batch", type=int, default=16,
                     help="N=8192 pairs per launch in the precision throughput report")
@@ -254,6 +254,75 @@ def cpu_baseline(x, y, seconds):
             "cpu": _cpu_model()}
 
 
+def _widen16(a):
+    if a.dtype == np.uint16:
+        return (a.astype(np.uint32) << 16).view(np.float32)
+    return a.astype(np.float32)
+
+
+def precision_errors(prec_maps, prec):
+    """CPU-baseline leg, outside every timed region: pair 0 of the precision
+    workload, as the timed FP32 / FP16 / BF16 launches computed it, against
+    the FP64 oracle -- on the stored (rounded) pixels (accumulation error) and
+    on the FP32 originals (storage + accumulation error) -- with the stated
+    storage bound (oracle.storage_bound, from the originals alone) checked on
+    every tile."""
+    import oracle
+    from oracle import storage_bound
+    orc = oracle.Oracle()
+    threads = (os.cpu_count() or 1) if orc.has_openmp else 1
+    x32, y32, maps = prec_maps
+    NT = 64
+    C1, C2, C, D = PARAMS["C1"], PARAMS["C2"], PARAMS["C"], PARAMS["D"]
+    ol, oa, osum = orc.maps(x32, y32, NT, C1, C2, C, D, threads=threads)
+    ol, oa = ol.ravel(), oa.ravel()
+    r32 = osum[:, 1] / (osum[:, 2] + osum[:, 3] + C)
+    for name, (x, y, gl, ga) in maps.items():
+        gl = gl.astype(np.float64).ravel()
+        ga = ga.astype(np.float64).ravel()
+        rl, ra, rsum = orc.maps(_widen16(x), _widen16(y), NT, C1, C2, C, D, threads=threads)
+        rl, ra = rl.ravel(), ra.ravel()
+        rr = rsum[:, 1] / (rsum[:, 2] + rsum[:, 3] + C)
+        nz = rl > 0
+        acc_l = np.abs(gl - rl)[nz] / rl[nz]
+        acc_a = np.abs(ga - ra) / np.maximum(np.abs(ra), rr)
+        nz32 = ol > 0
+        st_l = np.abs(gl - ol)[nz32] / ol[nz32]
+        st_a = np.abs(ga - oa) / np.maximum(np.abs(oa), r32)
+        lb, ab, _, _ = storage_bound.tile_bounds(x32, y32, NT, name, C1, C2, C, D)
+        ok = bool(np.all(np.abs(gl - ol) <= lb + 1e-5 * np.abs(rl)) and
+                  np.all(np.abs(ga - oa) <= ab + 1e-5 * np.maximum(np.abs(ra), rr)))
+        prec[name].update({
+            "acc_err_lisi_rel_max": float("%.3g" % acc_l.max()),
+            "acc_err_aug_max": float("%.3g" % acc_a.max()),
+            "storage_err_lisi_rel_median": float("%.3g" % np.median(st_l)),
+            "storage_err_lisi_rel_max": float("%.3g" % st_l.max()),
+            "storage_err_aug_max": float("%.3g" % st_a.max()),
+            "stated_bound_lisi_rel_max": float("%.3g" % np.max(lb[nz32] / ol[nz32])),
+            "stated_bound_aug_max": float("%.3g" % np.max(ab / np.maximum(np.abs(oa), r32))),
+            "within_stated_bound_every_tile": ok,
+        })
+    prec["errors"] = ("pair 0 of the timed launches against the FP64 oracle: acc_err on the "
+                      "stored pixels (bar 1e-5), storage_err on the FP32 originals; the "
+                      "stated storage bound (computed from the originals alone) plus the "
+                      "1e-5 accumulation bar checked on all %d tiles" % ol.size)
+
+
+def small_pair_errors(small, orc_threads=None):
+    """CPU-baseline leg: the small pair's GPU maps against the FP64 oracle."""
+    import oracle
+    orc = oracle.Oracle()
+    threads = orc_threads or ((os.cpu_count() or 1) if orc.has_openmp else 1)
+    x, y, gl, ga = small.pop("_maps")
+    C1, C2, C, D = PARAMS["C1"], PARAMS["C2"], PARAMS["C"], PARAMS["D"]
+    ol, oa, osum = orc.maps(x, y, 64, C1, C2, C, D, threads=threads)
+    ol, oa = ol.ravel(), oa.ravel()
+    r = osum[:, 1] / (osum[:, 2] + osum[:, 3] + C)
+    small["max_rel_err_lisi"] = float("%.3g" % np.max(np.abs(gl - ol) / ol))
+    small["max_rel_err_aug"] = float("%.3g" % np.max(np.abs(ga - oa) /
+                                                      np.maximum(np.abs(oa), r)))
+
+
 def _cpu_model():
     try:
         with open("/proc/cpuinfo") as f:
@@ -291,12 +360,98 @@ def _time_plan(iqa, ctx, plan, stream, K, warmup):
     return e0.elapsed_time(e1)
 
 
+def _isolated(stream, fn, count, delay_cycles=200000):
+    """Device times (us) of isolated launches: a GPU-side delay is queued
+    ahead of each, so the launch is already queued when the events run; the
+    first three are dropped."""
+    import torch
+    out = []
+    for i in range(count):
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(delay_cycles)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            fn(i)
+            a1.record(stream)
+        torch.cuda.synchronize()
+        out.append(a0.elapsed_time(a1) * 1e3)
+    return out[3:]
+
+
+def _region_mean(stream, fn, K, delay_cycles=100000):
+    """Mean device time (us) of an isolated launch from one event region:
+    K (delay, launch) pairs minus K delays alone, which averages out the
+    coarse tick of isolated event times."""
+    import torch
+    with torch.cuda.stream(stream):
+        for i in range(3):
+            torch.cuda._sleep(delay_cycles)
+            fn(i)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        for i in range(K):
+            torch.cuda._sleep(delay_cycles)
+            fn(i)
+        e[1].record(stream)
+        e[2].record(stream)
+        for i in range(K):
+            torch.cuda._sleep(delay_cycles)
+        e[3].record(stream)
+    torch.cuda.synchronize()
+    return (e[0].elapsed_time(e[1]) - e[2].elapsed_time(e[3])) * 1e3 / K
+
+
+def small_pair_report(iqa, ctx, params, stream):
+    """The small single pair (N=256, N_T=64, 16 tiles, FP32, 10 sources, seed
+    0): one iqa_both call, isolated (median of 10, the paper's count, and the
+    region mean) and back to back; its maps go to the CPU-baseline leg for
+    the error against the oracle."""
+    import torch
+    from paper_2501_10653_gb300 import synth
+    x, y = synth.small_pair()
+    N, NT = 256, 64
+    T = N // NT
+    dev = torch.device("cuda", torch.cuda.current_device())
+    # several copies, so that back-to-back launches rotate over distinct buffers
+    C = 8
+    dx = [torch.from_numpy(x).to(dev) for _ in range(C)]
+    dy = [torch.from_numpy(y).to(dev) for _ in range(C)]
+    lm = [torch.empty(T * T, device=dev) for _ in range(C)]
+    am = [torch.empty(T * T, device=dev) for _ in range(C)]
+    fn = lambda i: iqa.iqa_both(ctx, dx[i % C], dy[i % C], iqa.IQA_F32, N, NT, params,
+                                lm[i % C], am[i % C], None, stream)
+    iso = _isolated(stream, fn, 13)
+    mean = _region_mean(stream, fn, 40)
+    with torch.cuda.stream(stream):
+        for i in range(10):
+            fn(i)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(400):
+            fn(i)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    b2b = e0.elapsed_time(e1) * 1e3 / 400
+    return {"workload": "N=256 N_T=64 FP32 (16 tiles), 10 sources FWHM 3 px, flux 0.01..1, "
+                        "noise sigma 1e-3, 3 faintest dropped, seed 0; one iqa_both call "
+                        "per pair",
+            "single_launch_us_median10": round(float(np.median(iso)), 3),
+            "single_launch_us_mean": round(mean, 3),
+            "back_to_back_us_per_pair": round(b2b, 3),
+            "back_to_back_GBs": round(2 * N * N * 4 / (b2b * 1e-6) / 1e9, 1),
+            "launch": iqa.iqa_get_config(ctx, iqa.IQA_F32, N, NT, iqa.MAPS_BOTH).as_dict(),
+            "_maps": (x, y, lm[0].cpu().numpy().astype(np.float64),
+                      am[0].cpu().numpy().astype(np.float64))}
+
+
 def precision_report(iqa, ctx, params, stream, batch=16):
     """The precision workload's size (N=8192, N_T=64, point + extended sources,
     1e4 dynamic range, sigma 5e-3) stored as FP32, FP16 and BF16: the batched
-    throughput of each storage type.  (The per-tile error of each against the
-    FP64 oracle is measured and bounded by tests/test_gpu_precision.py; the
-    bench runs the oracle only as its CPU baseline.)"""
+    throughput of each storage type, and pair 0's maps from those launches
+    (returned apart: the per-tile errors against the FP64 oracle are formed
+    in the CPU-baseline leg, ``precision_errors``)."""
     import torch
     from paper_2501_10653_gb300 import synth
     N, NT = 8192, 64
@@ -306,6 +461,7 @@ def precision_report(iqa, ctx, params, stream, batch=16):
                        "flux 1e-4..1, noise sigma 5e-3, 10%% of sources dropped; %d copies of "
                        "the pair per launch" % batch}
     dev = torch.device("cuda", torch.cuda.current_device())
+    maps_out = {}
     for name, code in (("f32", iqa.IQA_F32), ("f16", iqa.IQA_F16), ("bf16", iqa.IQA_BF16)):
         x, y = synth._cast(x32.astype(np.float64), name), synth._cast(y32.astype(np.float64), name)
         tx = torch.from_numpy(x.view(np.int16) if x.dtype == np.uint16 else x).to(dev)
@@ -324,9 +480,12 @@ def precision_report(iqa, ctx, params, stream, batch=16):
             "batched_GBs": round(20 * B * 2 * N * N * es / (ms * 1e-3) / 1e9, 1),
             "pixel_pairs_per_s": round(20 * B * N * N / (ms * 1e-3), 1),
         }
+        # pair 0's maps, as the timed launches wrote them, for the error
+        # figures of the CPU-baseline leg
+        maps_out[name] = (x, y, outs[0][0].cpu().numpy(), outs[0][1].cpu().numpy())
         del xs, ys, outs, tx, ty
         torch.cuda.empty_cache()
-    return out
+    return out, (x32, y32, maps_out)
 
 
 def merge_report(iqa, params, ctx, stream, x, y, K=200):
@@ -606,31 +765,36 @@ def run_ours(args):
     for p in one_plans:
         iqa.iqa_plan_destroy(p)
     def single_launches(fn, count):
-        """Device time of `count` isolated launches (a GPU-side delay queued
-        ahead of each, so the launch is already queued when the events run);
-        successive launches rotate over the B pairs, so a launch's pixels were
-        last touched B - 1 pairs (far more than L2) earlier."""
-        out = []
-        for i in range(count):
-            with torch.cuda.stream(stream):
-                torch.cuda._sleep(200000)
-                a0 = torch.cuda.Event(enable_timing=True)
-                a1 = torch.cuda.Event(enable_timing=True)
-                a0.record(stream)
-                fn(i % B)
-                a1.record(stream)
-            torch.cuda.synchronize()
-            out.append(a0.elapsed_time(a1) * 1e3)
-        return out[3:]
+        return _isolated(stream, lambda i: fn(i % B), count)
 
-    single = single_launches(lambda j: iqa.iqa_both(ctx, dx[j], dy[j], iqa.IQA_F32, N, NT,
-                                                    params, lisi[j], aug[j], None, stream), 63)
+    both_j = lambda j: iqa.iqa_both(ctx, dx[j], dy[j], iqa.IQA_F32, N, NT, params, lisi[j],
+                                    aug[j], None, stream)
+    single = single_launches(both_j, 63)
     single_us = float(np.median(single))
+    single_mean = _region_mean(stream, lambda i: both_j(i % B), 60)
     lisi_only = single_launches(lambda j: iqa.iqa_lisi(ctx, dx[j], dy[j], iqa.IQA_F32, N, NT,
                                                        params, lisi[j], None, stream), 13)
     aug_only = single_launches(lambda j: iqa.iqa_auglisi(ctx, dx[j], dy[j], iqa.IQA_F32, N, NT,
                                                          params, aug[j], None, stream), 13)
     plain_cfg = iqa.iqa_get_config(ctx, iqa.IQA_F32, N, NT, iqa.MAPS_BOTH).as_dict()
+    # the floor of this way of timing: an empty kernel, isolated the same way
+    floor = _isolated(stream, lambda i: torch.cuda._sleep(1), 23)
+    floor_mean = _region_mean(stream, lambda i: torch.cuda._sleep(1), 60)
+    # the paper's other timing form: one pair per call at every N_T of the sweep
+    nt_single = {}
+    for nt in PAPER_NT_SWEEP:
+        t2 = N // nt
+        lm2 = [torch.empty(t2 * t2, device=dev) for _ in range(2)]
+        am2 = [torch.empty(t2 * t2, device=dev) for _ in range(2)]
+        fn = (lambda nt_, lm_, am_: lambda i: iqa.iqa_both(
+            ctx, dx[i % B], dy[i % B], iqa.IQA_F32, N, nt_, params, lm_[i % 2], am_[i % 2],
+            None, stream))(nt, lm2, am2)
+        iso = _isolated(stream, fn, 13)
+        nt_single[str(nt)] = {"median10_us": round(float(np.median(iso)), 3),
+                              "mean_us": round(_region_mean(stream, fn, 40), 3),
+                              "launch": iqa.iqa_get_config(ctx, iqa.IQA_F32, N, nt,
+                                                           iqa.MAPS_BOTH).as_dict()}
+    small = small_pair_report(iqa, ctx, params, stream)
 
     # N_T sweep of the batched form (the paper's Fig. 1 axis)
     sweep = {}
@@ -667,9 +831,9 @@ def run_ours(args):
             "tuned": tuned16}
         del hx16, hy16
 
-    prec = None
+    prec, prec_maps = None, None
     if rank == 0 and world == 1 and not args.no_precision:
-        prec = precision_report(iqa, ctx, params, stream, args.precision_batch)
+        prec, prec_maps = precision_report(iqa, ctx, params, stream, args.precision_batch)
 
     # N sweep at N_T = 64 (the paper's other Fig. 1 axis), about the same bytes
     # per launch at every N, built on the device from the step's pairs:
@@ -763,6 +927,11 @@ def run_ours(args):
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             cpu = cpu_baseline(host_pairs[0][0], host_pairs[0][1], args.cpu_seconds)
+            # error figures against the oracle (outside every timed region)
+            small_pair_errors(small)
+            if prec_maps is not None:
+                precision_errors(prec_maps, prec)
+        small.pop("_maps", None)
         result = {
             "metric": METRIC, "value": round(value, 2), "unit": "GB/s",
             "n_gpus": world, "steps": K, "warmup": max(3, args.warmup),
@@ -794,17 +963,24 @@ def run_ours(args):
                 "single_launch_us_median60": round(single_us, 3),
                 "single_launch_us_min": round(float(np.min(single)), 3),
                 "single_launch_us_mean": round(float(np.mean(single)), 3),
+                "single_launch_us_mean_of_60_in_one_region": round(single_mean, 3),
+                "empty_kernel_single_launch_us_median": round(float(np.median(floor)), 3),
+                "empty_kernel_single_launch_us_mean_of_60": round(floor_mean, 3),
+                "nt_sweep_single_launch": nt_single,
                 "lisi_only_single_us_median10": round(float(np.median(lisi_only)), 3),
                 "auglisi_only_single_us_median10": round(float(np.median(aug_only)), 3),
                 "launch": plain_cfg,
                 "independent_plans_us_per_pair": round(plan_pair_us, 3),
                 "independent_plans_GBs": round(pair_bytes / (plan_pair_us * 1e-6) / 1e9, 1),
                 "timing": "back-to-back iqa_both launches replayed from a CUDA graph; "
-                          "single launches (60 of both maps, 10 of each map alone) each "
-                          "with a GPU-side delay queued ahead, rotating over the step's "
-                          "pairs so that no launch finds its pixels in L2; isolated event "
-                          "times are quantised to about 2 us on this GPU, so the mean of 60 "
-                          "is the finer figure"},
+                          "single launches (60 of both maps, 10 of each map alone, 10 per "
+                          "N_T) each with a GPU-side delay queued ahead, rotating over the "
+                          "step's pairs so that no launch finds its pixels in L2; isolated "
+                          "event times are quantised to about 2 us on this GPU, so the "
+                          "region mean (60 delay+launch pairs in one event region, minus 60 "
+                          "delays alone) is the finer figure; the empty kernel timed both "
+                          "ways is the floor of the method (launch and event overhead)"},
+            "small_pair_N256": small,
             "nt_sweep_GBs": sweep,
             "n_sweep_NT64": nsweep,
             "storage_16bit": storage16,
