@@ -453,7 +453,7 @@ typedef struct {
 typedef struct {
     iqa_dtype dtype;           /* storage of references and epochs */
     int max_pairs_per_step;    /* 1..64 */
-    int max_inflight_steps;    /* 1..4 */
+    int max_inflight_steps;    /* 1..8 */
     size_t pool_bytes;         /* device memory for second epochs: the admission
                                   budget (a request needs N*N elements) */
     int one_pair_per_launch;   /* 1: the plain path as a baseline -- one request
@@ -470,6 +470,16 @@ typedef struct {
                                   large request does not hold small ones back;
                                   0 = no cap */
     iqa_params params;
+    int generator_blocks_per_sm; /* resident epoch-generator blocks per SM,
+                                  1..8 (0 = 8, every SM full): fewer leave
+                                  room for other steps' map kernels */
+    int map_ctas_per_sm;       /* persistent map-kernel CTAs per SM, 1..4
+                                  (0 = the context's batched shape) */
+    int time_kernels;          /* 1: timing marks around each step's generator
+                                  and map kernel (the mean_step_* and *_per_pair
+                                  statistics); they cut the launch overlap
+                                  between the two kernels, adding about 10 us
+                                  to a small step's latency, so 0 by default */
 } iqa_server_config;
 
 typedef struct {
@@ -494,6 +504,12 @@ typedef struct {
      * the start of its step's launch calls (queueing), the launch calls
      * themselves (host), and the rest (device work, read-back, detection) */
     double p50_queue_ms, p50_launch_ms, p50_device_ms;
+    /* device time of the steps' two kernels, from timing marks around them
+     * in each step (the epoch generator, then the map kernel): means per step
+     * and per completed pair; 0 unless the server was created with
+     * time_kernels = 1 */
+    double mean_step_generator_ms, mean_step_map_ms;
+    double generator_ms_per_pair, map_ms_per_pair;
 } iqa_server_stats;
 
 /* Creates a server on ctx's device (ctx may be NULL with simulate = 1) and

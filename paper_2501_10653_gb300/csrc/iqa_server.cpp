@@ -132,6 +132,9 @@ struct Slot {
     Clock::time_point t_launch;
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
+    // timing marks of the step's device work: before the epoch generator,
+    // between it and the map kernel, after the map kernel
+    cudaEvent_t mark[3] = {nullptr, nullptr, nullptr};
     // the step's work tables, one block in page-locked memory and its device
     // copy (one upload per step): generator header {njobs, total_bins}, map
     // kernel header {npairs, total_units}, generator jobs, pair descriptors
@@ -192,6 +195,9 @@ struct iqa_server {
     // rest (device work, read-back and completion detection)
     std::vector<double> lat_queue, lat_launch, lat_device;
     double bytes_done = 0.0;
+    // summed device time of the steps' generator and map kernels
+    double gen_ms = 0.0, map_ms = 0.0;
+    long long marked_steps = 0, marked_pairs = 0;
     bool have_first = false;
     Clock::time_point t_first, t_last;
     std::string worker_error;
@@ -218,6 +224,8 @@ void free_slot(Slot &s)
     cudaFreeHost(const_cast<int *>(s.h_status));
     cudaFreeHost(s.h_out);
     if (s.ev) cudaEventDestroy(s.ev);
+    for (cudaEvent_t m : s.mark)
+        if (m) cudaEventDestroy(m);
     if (s.st) cudaStreamDestroy(s.st);
     s = Slot();
 }
@@ -252,12 +260,19 @@ cudaError_t capture_slot(iqa_server *srv, Slot &s)
         if (e != cudaSuccess) return e;
         cudaError_t e1 =
             cudaMemcpyAsync(s.d_tab, s.h_tab, s.tab_bytes, cudaMemcpyHostToDevice, s.st);
+        const bool marks = srv->cfg.time_kernels != 0;
+        if (e1 == cudaSuccess && marks)
+            e1 = cudaEventRecordWithFlags(s.mark[0], s.st, cudaEventRecordExternal);
         if (e1 == cudaSuccess)
             e1 = launch_synth((int)srv->cfg.dtype, s.d_jobs, s.d_synth_hdr, sgrid, s.st);
+        if (e1 == cudaSuccess && marks)
+            e1 = cudaEventRecordWithFlags(s.mark[1], s.st, cudaEventRecordExternal);
         if (e1 == cudaSuccess) {
             StreamParams sp = slot_stream_params(srv, s);
             e1 = launch_stream(sp, srv->cfg.dtype, srv->kcfg, MAPS_AB, grid, s.st);
         }
+        if (e1 == cudaSuccess && marks)
+            e1 = cudaEventRecordWithFlags(s.mark[2], s.st, cudaEventRecordExternal);
         e = cudaStreamEndCapture(s.st, &s.graph[g]);
         if (e1 != cudaSuccess) return e1;
         if (e != cudaSuccess) return e;
@@ -272,6 +287,7 @@ cudaError_t alloc_slot(iqa_server *srv, Slot &s)
     const int M = srv->cfg.max_pairs_per_step;
     cudaError_t e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
+    for (int m = 0; m < 3 && e == cudaSuccess; ++m) e = cudaEventCreate(&s.mark[m]);
     // table block: headers at 0 and 16, jobs at 64, descriptors 64-aligned
     const size_t off_jobs = 64;
     const size_t off_pairs = round_up(off_jobs + sizeof(SynthJob) * M, 64);
@@ -403,8 +419,11 @@ iqa_status launch_step(iqa_server *srv, Slot &s)
         e = cudaMemcpyAsync(s.d_tab, s.h_tab,
                             reinterpret_cast<unsigned char *>(s.h_jobs + 1) - s.h_tab,
                             cudaMemcpyHostToDevice, s.st);
+        const bool marks = srv->cfg.time_kernels != 0;
+        if (e == cudaSuccess && marks) e = cudaEventRecord(s.mark[0], s.st);
         if (e == cudaSuccess)
             e = launch_synth((int)srv->cfg.dtype, s.d_jobs, s.d_synth_hdr, srv->synth_grid, s.st);
+        if (e == cudaSuccess && marks) e = cudaEventRecord(s.mark[1], s.st);
         if (e == cudaSuccess) {
             TileConfig c = pick_config(ctx, r.N, r.r.NT, srv->cfg.dtype, MAPS_AB, true);
             if (c.variant == 1) {
@@ -419,6 +438,7 @@ iqa_status launch_step(iqa_server *srv, Slot &s)
                 e = launch_tiles(a, c, srv->cfg.dtype, MAPS_AB, r.T, s.st);
             }
         }
+        if (e == cudaSuccess && marks) e = cudaEventRecord(s.mark[2], s.st);
     } else {
         int g = 0;
         while (g < 3 && s.grid[g] < units) ++g;
@@ -491,6 +511,19 @@ void retire(iqa_server *srv, Slot &s)
         return;
     }
     const auto now = Clock::now();
+    if (st == IQA_OK && !srv->cfg.simulate && srv->cfg.time_kernels) {
+        // device time of the step's two kernels, from its timing marks
+        float gen = 0.0f, map = 0.0f;
+        if (cudaEventElapsedTime(&gen, s.mark[0], s.mark[1]) == cudaSuccess &&
+            cudaEventElapsedTime(&map, s.mark[1], s.mark[2]) == cudaSuccess) {
+            srv->gen_ms += gen;
+            srv->map_ms += map;
+            ++srv->marked_steps;
+            srv->marked_pairs += (long long)s.reqs.size();
+        } else {
+            cudaGetLastError();
+        }
+    }
     size_t o = 0;
     for (auto &rp : s.reqs) {
         Request &r = *rp;
@@ -799,10 +832,14 @@ iqa_status iqa_server_create(iqa_ctx *ctx, const iqa_server_config *cfg, iqa_ser
     *out = nullptr;
     if (!cfg->simulate && !ctx) return IQA_ERR_INVALID_ARG;
     if (!dtype_ok(cfg->dtype) || cfg->max_pairs_per_step < 1 || cfg->max_pairs_per_step > 64 ||
-        cfg->max_inflight_steps < 1 || cfg->max_inflight_steps > 4 || cfg->pool_bytes < 256 ||
-        cfg->simulate < 0 || cfg->simulate > 2 || !(cfg->step_timeout_ms >= 0)) {
+        cfg->max_inflight_steps < 1 || cfg->max_inflight_steps > 8 || cfg->pool_bytes < 256 ||
+        cfg->simulate < 0 || cfg->simulate > 2 || !(cfg->step_timeout_ms >= 0) ||
+        cfg->generator_blocks_per_sm < 0 || cfg->generator_blocks_per_sm > kSynthBlocksPerSM ||
+        cfg->map_ctas_per_sm < 0 || cfg->map_ctas_per_sm > 4 || cfg->time_kernels < 0 ||
+        cfg->time_kernels > 1) {
         set_error(ctx, "bad server config (max_pairs_per_step 1..64, max_inflight_steps "
-                       "1..4, pool_bytes > 0)");
+                       "1..8, pool_bytes > 0, generator_blocks_per_sm 0..8, "
+                       "map_ctas_per_sm 0..4, time_kernels 0..1)");
         return IQA_ERR_INVALID_ARG;
     }
     iqa_params P;
@@ -826,8 +863,21 @@ iqa_status iqa_server_create(iqa_ctx *ctx, const iqa_server_config *cfg, iqa_ser
         // batched form's 16-bit default) spread a small request over more CTAs
         // (served p50 0.079 against 0.089 ms with 32K units)
         srv->kcfg.unit_kpx = 16;
+        if (cfg->map_ctas_per_sm > 0) {
+            TileConfig k = srv->kcfg;
+            k.ctas_per_sm = cfg->map_ctas_per_sm;
+            std::string why;
+            // the shape's shared memory must fit the requested CTAs per SM
+            if (!stream_config_valid(1024, 64, cfg->dtype, k, &why)) {
+                set_error(ctx, "map_ctas_per_sm %d: %s", cfg->map_ctas_per_sm, why.c_str());
+                return IQA_ERR_INVALID_ARG;
+            }
+            srv->kcfg = k;
+        }
         srv->device = ctx->device;
-        srv->synth_grid = ctx->num_sms * kSynthBlocksPerSM;
+        srv->synth_grid = ctx->num_sms * (cfg->generator_blocks_per_sm > 0
+                                              ? cfg->generator_blocks_per_sm
+                                              : kSynthBlocksPerSM);
         int prev = 0;
         cudaGetDevice(&prev);
         cudaSetDevice(ctx->device);
@@ -1125,6 +1175,12 @@ iqa_status iqa_server_get_stats(iqa_server *srv, iqa_server_stats *out)
         out->p50_queue_ms = median(srv->lat_queue);
         out->p50_launch_ms = median(srv->lat_launch);
         out->p50_device_ms = median(srv->lat_device);
+        if (srv->marked_steps) {
+            out->mean_step_generator_ms = srv->gen_ms / srv->marked_steps;
+            out->mean_step_map_ms = srv->map_ms / srv->marked_steps;
+            out->generator_ms_per_pair = srv->gen_ms / srv->marked_pairs;
+            out->map_ms_per_pair = srv->map_ms / srv->marked_pairs;
+        }
         const double span_s = ms_between(srv->t_first, srv->t_last) / 1e3;
         if (span_s > 0) {
             out->pairs_per_s = srv->completed / span_s;

@@ -92,7 +92,9 @@ class iqa_server_config(ctypes.Structure):
                 ("max_inflight_steps", ctypes.c_int), ("pool_bytes", ctypes.c_size_t),
                 ("one_pair_per_launch", ctypes.c_int), ("simulate", ctypes.c_int),
                 ("sim_bytes_per_s", ctypes.c_double), ("step_timeout_ms", ctypes.c_double),
-                ("max_step_bytes", ctypes.c_ulonglong), ("params", iqa_params)]
+                ("max_step_bytes", ctypes.c_ulonglong), ("params", iqa_params),
+                ("generator_blocks_per_sm", ctypes.c_int), ("map_ctas_per_sm", ctypes.c_int),
+                ("time_kernels", ctypes.c_int)]
 
 
 class iqa_request(ctypes.Structure):
@@ -113,7 +115,11 @@ class iqa_server_stats(ctypes.Structure):
                 ("mean_pairs_per_step", ctypes.c_double),
                 ("pool_bytes", ctypes.c_ulonglong), ("pool_peak_bytes", ctypes.c_ulonglong),
                 ("p50_queue_ms", ctypes.c_double), ("p50_launch_ms", ctypes.c_double),
-                ("p50_device_ms", ctypes.c_double)]
+                ("p50_device_ms", ctypes.c_double),
+                ("mean_step_generator_ms", ctypes.c_double),
+                ("mean_step_map_ms", ctypes.c_double),
+                ("generator_ms_per_pair", ctypes.c_double),
+                ("map_ms_per_pair", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -411,14 +417,16 @@ class _Server:
 def iqa_server_create(ctx, dtype=IQA_F16, max_pairs_per_step=16, max_inflight_steps=2,
                       pool_bytes=8 << 30, one_pair_per_launch=0, simulate=0,
                       sim_bytes_per_s=1e12, step_timeout_ms=0.0, max_step_bytes=0,
-                      params=None):
+                      params=None, generator_blocks_per_sm=0, map_ctas_per_sm=0,
+                      time_kernels=0):
     p = iqa_params(1e-6, 1e-6, 1e-6, 0.0) if params is None else params
     if isinstance(p, dict):
         p = iqa_params(p.get("C1", 1e-6), p.get("C2", 1e-6), p.get("C", 1e-6), p.get("D", 0.0))
     cfg = iqa_server_config(int(dtype), int(max_pairs_per_step), int(max_inflight_steps),
                             int(pool_bytes), int(one_pair_per_launch), int(simulate),
                             float(sim_bytes_per_s), float(step_timeout_ms),
-                            int(max_step_bytes), p)
+                            int(max_step_bytes), p, int(generator_blocks_per_sm),
+                            int(map_ctas_per_sm), int(time_kernels))
     h = _vp()
     _check(ctx, lib().iqa_server_create(ctx, ctypes.byref(cfg), ctypes.byref(h)))
     return _Server(ctx, h.value)

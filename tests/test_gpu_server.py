@@ -74,7 +74,7 @@ def test_served_maps_against_oracle(ctx, orc):
     """Requests of mixed N and N_T, with drops and a transient, served in
     batched steps: each map against the oracle on host-mirrored inputs."""
     from paper_2501_10653_gb300 import iqa
-    srv, cats = _server(ctx, iqa.IQA_F16)
+    srv, cats = _server(ctx, iqa.IQA_F16, time_kernels=1)
     reqs = [(0, 32, 11, [0], None), (1, 64, 12, [1, 3], (2, 700, 300, 0.8)),
             (2, 128, 13, [4, 5, 6], None), (2, 64, 14, [], (0, 1500, 99, 0.05)),
             (1, 32, 15, [2], None), (0, 128, 16, [1], (1, 20, 400, 1.5))]
@@ -91,6 +91,11 @@ def test_served_maps_against_oracle(ctx, orc):
             y = synth.render_epoch(cats[rid], seed, drop=drop, add=add, dtype="f16")
             ol, oa, osum = parity.oracle_maps(orc, x, y, NT, PARAMS)
             parity.assert_parity((l, a, None), (ol, oa, osum), PARAMS)
+        # every step's two kernels were timed by the marks around them
+        st = iqa.iqa_server_get_stats(srv)
+        assert st.mean_step_generator_ms > 0 and st.mean_step_map_ms > 0
+        assert st.generator_ms_per_pair <= st.mean_step_generator_ms
+        assert st.map_ms_per_pair <= st.mean_step_map_ms
     finally:
         iqa.iqa_server_destroy(srv)
 
@@ -123,7 +128,7 @@ def test_same_result_alone_and_in_the_mix(ctx):
 
 def test_one_pair_per_launch_baseline_against_oracle(ctx, orc):
     from paper_2501_10653_gb300 import iqa
-    srv, cats = _server(ctx, iqa.IQA_F32, one_pair_per_launch=1)
+    srv, cats = _server(ctx, iqa.IQA_F32, one_pair_per_launch=1, time_kernels=1)
     try:
         reqs = [(0, 64, 31, [1]), (2, 32, 32, [0, 3]), (1, 128, 33, [])]
         hs = [iqa.iqa_submit(srv, iqa.make_request(r, nt, sd, dr)) for r, nt, sd, dr in reqs]
@@ -137,6 +142,7 @@ def test_one_pair_per_launch_baseline_against_oracle(ctx, orc):
             parity.assert_parity((l, a, None), (ol, oa, osum), PARAMS)
         st = iqa.iqa_server_get_stats(srv)
         assert st.mean_pairs_per_step == pytest.approx(1.0)
+        assert st.mean_step_generator_ms > 0 and st.mean_step_map_ms > 0
     finally:
         iqa.iqa_server_destroy(srv)
 
