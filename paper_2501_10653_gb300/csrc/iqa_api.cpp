@@ -235,20 +235,45 @@ static TileConfig fit_one_wave(iqa_ctx *ctx, int N, int NT, iqa_dtype dtype, int
     if (c.variant != 0 || c.S != 1 || c.vec == 1) return c;
     const int T = N / NT;
     const long long sms = ctx->num_sms > 0 ? ctx->num_sms : 152;
-    const long long units = (long long)(T / c.TX) * T;
-    const int occ = tiles_occupancy(ctx, dtype, c, maps);
-    if (occ <= 0 || units <= occ * sms || units > 2 * occ * sms) return c;
     const int LPT = NT / c.vec;
-    for (int tx = c.TX + 1; tx <= std::min(T, kMaxTX); ++tx) {
-        if (T % tx || tx % c.TX) continue;
-        const long long lpu = (long long)tx * LPT;
-        if (lpu > c.threads || c.threads % lpu) continue;
+    const auto ilp_for = [&](const TileConfig &w) {
+        const long long per_thread = (long long)NT * w.TX * LPT / w.threads;
+        return per_thread >= 8 ? 8 : per_thread >= 4 ? 4 : 2;
+    };
+    long long units = (long long)(T / c.TX) * T;
+    int occ = tiles_occupancy(ctx, dtype, c, maps);
+    if (occ <= 0) return c;
+    if (units > occ * sms && units <= 2 * occ * sms) {
+        for (int tx = c.TX + 1; tx <= std::min(T, kMaxTX); ++tx) {
+            if (T % tx || tx % c.TX) continue;
+            const long long lpu = (long long)tx * LPT;
+            if (lpu > c.threads || c.threads % lpu) continue;
+            TileConfig w = c;
+            w.TX = tx;
+            w.ilp = ilp_for(w);
+            const int occ_w = tiles_occupancy(ctx, dtype, w, maps);
+            if (occ_w > 0 && (long long)(T / tx) * T <= occ_w * sms) {
+                c = w;
+                units = (long long)(T / tx) * T;
+                occ = occ_w;
+                break;
+            }
+        }
+    }
+    // A grid that fills at most half of the resident slots leaves load
+    // slots unused: wider CTAs put more loads in flight at once, as long as
+    // every thread keeps a full batch of 8 vectors and the grid still fits
+    // one wave (N=2048, N_T=128: 256 CTAs of 256 threads, 8.3 against 10.2 us
+    // per isolated launch).
+    while (c.threads < 512 && 2 * units <= occ * sms) {
         TileConfig w = c;
-        w.TX = tx;
-        long long per_thread = (long long)NT * lpu / w.threads;
-        w.ilp = per_thread >= 8 ? 8 : per_thread >= 4 ? 4 : 2;
+        w.threads = c.threads * 2;
+        if ((long long)NT * c.TX * LPT / w.threads < 8) break;
+        w.ilp = ilp_for(w);
         const int occ_w = tiles_occupancy(ctx, dtype, w, maps);
-        if (occ_w > 0 && (long long)(T / tx) * T <= occ_w * sms) return w;
+        if (occ_w <= 0 || units > occ_w * sms) break;
+        c = w;
+        occ = occ_w;
     }
     return c;
 }
