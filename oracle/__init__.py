@@ -13,10 +13,14 @@ Contents
   the per-tile values and the per-tile pixel sums.
 * ``merge_tiles``: Eq. 3 / Eq. 4 applied to every m x m block of tiles.
 * ``exact``: an exact-rational brute force of Eq. 1 / Eq. 2 for tiny inputs.
+* ``storage_bound``: a bound, from the FP32 originals alone, on how far Eq. 1
+  and Eq. 2 move when the pixels are stored in FP16 or BF16.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (hand-derived golden values, closed forms, the Eq. 3 / Eq. 4 identities, tile
-markers, invariants) and by ``tests/test_oracle_mutants.py``.
+markers, invariants) and by ``tests/test_oracle_mutants.py``; the storage bound
+by ``tests/test_storage_bound.py`` (against the oracle on the original and the
+rounded pixels, including a hand-computed rounding tie).
 """
 import ctypes
 import os
