@@ -7,8 +7,8 @@
 //     first, then grabs of consecutive units from a global counter (about
 //     64 KB per image each, fetched one grab ahead, shrinking toward one unit
 //     as the work runs out), or round-robin without a counter; the producer
-//     tells the consumers which unit and pair a stage holds through per-stage
-//     slots in shared memory;
+//     tells the consumers which pair a stage holds and the first tile of its
+//     unit through per-stage slots in shared memory;
 //   * a producer warp streams every unit in chunks of CH rows with TMA tensor
 //     copies (cp.async.bulk.tensor: one 2-D box, or one 3-D box of 256-element
 //     segments for rows wider than 256) of x and y into a ring of shared-
@@ -201,7 +201,8 @@ __device__ __forceinline__ void write_tile_desc(const PairDesc &d, long long t, 
 }
 
 // Dynamic shared memory layout: [stages][2][stage_bytes] ring, then the
-// 2*stages mbarriers, the per-stage unit slots, the reduction scratch
+// 2*stages mbarriers, the per-stage slots (first tile of the stage's unit
+// within its pair, -1 at the end of work; the pair's index), the reduction scratch
 // red[4][CT] and part[kMaxTX*4], and the abort flag.  Host:
 // stream_smem_bytes().
 template <typename T, int CT, bool DO_A, bool DO_B>
@@ -245,6 +246,8 @@ __global__ void __launch_bounds__(CT + 32, 1)
         // ---------------- producer warp: one elected lane issues the copies
         if (tid != CT) return;
         long long k = 0;  // chunk counter of this CTA
+        int ps = 0;         // its stage, k % S
+        uint32_t pph = 1u;  // the empty-barrier parity to wait on, ((k / S) & 1) ^ 1
         int last_pair = -1;
         bool ok = true;
         // Work is taken in grabs of consecutive units [u, u_end): one
@@ -271,8 +274,15 @@ __global__ void __launch_bounds__(CT + 32, 1)
         const auto fetch_next = [&](uint32_t unit_bytes) {
             if (sp.sched) {
                 unsigned g = unit_bytes >= kGrabBytes ? 1u : min(8u, kGrabBytes / unit_bytes);
-                const long long share = (total_units - u) / (4LL * gridDim.x);
-                if (share < (long long)g) g = (unsigned)(share > 1 ? share : 1);
+                // guided: at most a quarter of this CTA's share of what is left,
+                // (total_units - u) / (4 gridDim.x), tested without a 64-bit
+                // division (floor(a / b) < g exactly when a < g b)
+                const long long left = total_units - u;
+                const long long span = 4LL * gridDim.x;
+                if (left < (long long)g * span) {
+                    const unsigned share = left > 0 ? (unsigned)left / (unsigned)span : 0u;
+                    g = share > 1 ? share : 1u;
+                }
                 nxt = (long long)gridDim.x +
                       (long long)atomicAdd(&sp.sched[0], (unsigned long long)g);
                 nxt_end = nxt + g;
@@ -303,6 +313,7 @@ __global__ void __launch_bounds__(CT + 32, 1)
             const PairDesc &d = descs[pi];
             const int nchunks = last ? 1 : d.chunks;
             int col0 = 0, row0 = 0;
+            long long t0 = -1;  // first tile of the unit within its pair
             uint32_t bytes = 0;
             if (!last) {
                 if (pi != last_pair) {
@@ -315,15 +326,23 @@ __global__ void __launch_bounds__(CT + 32, 1)
                     last_pair = pi;
                 }
                 const long long lu = u - d.unit_begin;
-                const int trow = (int)(lu / d.units_x);
-                col0 = (int)(lu - (long long)trow * d.units_x) * d.TX * d.NT;
+                // a 32-bit division whenever the unit index fits (every pair
+                // below 2^31 units): the 64-bit one is a long subroutine
+                const int trow = lu <= (long long)INT_MAX ? (int)lu / d.units_x
+                                                          : (int)(lu / d.units_x);
+                const int ucol = (int)(lu - (long long)trow * d.units_x);
+                col0 = ucol * d.TX * d.NT;
                 row0 = trow * d.NT;
+                t0 = (long long)trow * d.T + (long long)ucol * d.TX;
                 bytes = (uint32_t)(d.CH * d.TX * d.NT * (int)sizeof(T));
                 if (!have_next && waited) fetch_next(bytes * (uint32_t)d.chunks);
             }
             for (int c = 0; c < nchunks; ++c, ++k) {
-                const int s = (int)(k % S);
-                const uint32_t par = (uint32_t)((k / S) & 1) ^ 1u;
+                // ring position of chunk k: stage k % S, and the parity of the
+                // empty barrier's phase to wait on, ((k / S) & 1) ^ 1, kept
+                // incrementally (no division per chunk)
+                const int s = ps;
+                const uint32_t par = pph;
                 if (!mbar_wait(&empty[s], par, sp.timeout_ns)) {
                     if (sp.status) atomicOr(sp.status, STREAM_TIMEOUT_EMPTY);
                     atomicExch(abort_flag, 1);
@@ -350,7 +369,7 @@ __global__ void __launch_bounds__(CT + 32, 1)
                     ok = false;
                     break;
                 }
-                stage_unit[s] = u;
+                stage_unit[s] = t0;
                 stage_pair[s] = pi;
                 mbar_expect_tx(&full[s], 2 * bytes);
                 unsigned char *dst = ring + (size_t)s * 2 * SB;
@@ -360,6 +379,10 @@ __global__ void __launch_bounds__(CT + 32, 1)
                 } else {
                     tma_load_2d(dst, &d.tmx, col0, row0 + c * d.CH, &full[s]);
                     tma_load_2d(dst + SB, &d.tmy, col0, row0 + c * d.CH, &full[s]);
+                }
+                if (++ps == S) {
+                    ps = 0;
+                    pph ^= 1u;
                 }
             }
             if (!waited) {
@@ -403,24 +426,27 @@ __global__ void __launch_bounds__(CT + 32, 1)
     // thread is ever left waiting at a barrier the others skipped.
     const int lane = tid & 31;
     const PairDesc *d = nullptr;
-    long long u = -1, lu = 0;
+    long long t0 = -1;  // first tile of the current unit within its pair
     int c = 0, V = 0, chunks = 0;
     float C1f = 0.0f;
     Kahan ka, kb, kx, ky;
-    for (long long k = 0;; ++k) {
-        const int s = (int)(k % S);
-        if (!mbar_wait(&full[s], (uint32_t)((k / S) & 1), sp.timeout_ns)) {
+    // ring position of chunk k: stage s = k % S, full-barrier parity
+    // ph = (k / S) & 1, kept incrementally (no division per chunk)
+    int s = 0;
+    uint32_t ph = 0u;
+    for (;;) {
+        if (!mbar_wait(&full[s], ph, sp.timeout_ns)) {
             if (sp.status) atomicOr(sp.status, STREAM_TIMEOUT_FULL);
             atomicExch(abort_flag, 1);
         }
         named_bar(2, CT);
         if (*((volatile int *)abort_flag)) return;
         if (c == 0) {
-            // a new unit: its descriptor fields are read once into registers
-            u = stage_unit[s];
-            if (u < 0) return;
+            // a new unit: its first tile (the producer formed it) and its
+            // descriptor fields are read once into registers
+            t0 = stage_unit[s];
+            if (t0 < 0) return;
             d = &descs[stage_pair[s]];
-            lu = u - d->unit_begin;
             V = d->CH * d->LPU;
             chunks = d->chunks;
             C1f = d->C1f;
@@ -480,13 +506,14 @@ __global__ void __launch_bounds__(CT + 32, 1)
             const int TX = d->TX, LPU = d->LPU, LPT = d->LPT;
             float acc[4] = {ka.value(), kb.value(), kx.value(), ky.value()};
             reduce_unit<CT>(acc, TX, LPU, LPT, red, part, NamedBarrier<1, CT>());
-            const int trow = (int)(lu / d->units_x);
-            const int ucol = (int)(lu - (long long)trow * d->units_x);
-            const long long t0 = (long long)trow * d->T + (long long)ucol * TX;
             const bool out_ok = IQA_CHECK(t0 + TX <= (long long)d->T * d->T && TX <= kMaxTX);
             for (int tl = tid; tl < TX && out_ok; tl += CT)
                 write_tile_desc(*d, t0 + tl, part[tl * 4 + 0], part[tl * 4 + 1],
                                 part[tl * 4 + 2], part[tl * 4 + 3]);
+        }
+        if (++s == S) {
+            s = 0;
+            ph ^= 1u;
         }
     }
 }
