@@ -45,18 +45,20 @@ PARAMS = {"C1": 1e-6, "C2": 1e-6, "C": 1e-6, "D": 0.5e-6}
 PAPER_NT_SWEEP = (16, 32, 64, 128, 256)
 PAPER_N_SWEEP = (512, 1024, 2048, 4096, 8192)
 
-# DRAM traffic of the timed kernel from one ncu capture (summary and command in
-# profiles/iqa_stream_kernel_N2048_NT64_batch8_f32.md): dram__bytes_read.sum +
-# dram__bytes_write.sum of a launch over 8 pairs, per pair.  Valid only for the
-# kernel sources it was taken on: `traffic` is reported as null when their
-# hash no longer matches.
+# DRAM traffic of the timed kernel from one ncu capture of the timed launch
+# itself (summary and command in profiles/iqa_stream_kernel_N2048_NT64_batch32_f32.md):
+# dram__bytes_read.sum + dram__bytes_write.sum of the first launch inside the
+# headline_timed NVTX range, 32 pairs.  Valid only for the kernel sources it was
+# taken on: `traffic` is reported as null when their hash no longer matches.
 PROFILED_TRAFFIC = {
     "sources": ["paper_2501_10653_gb300/csrc/iqa_device.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream_f32.cu"],
-    "sha256": "b1ae99b7dc54853690693fe6181f5d594d7b002f313900566acdaadab972ca8f",
-    "bytes_per_pair": (268494080 + 3379456) / 8,
-    "capture": "8 pairs per launch, scaled by pairs to the timed launch",
+    "sha256": "5a26356ce9ee19ea1e4da53b6a39774b55dc01b4ad79ad9810befdb7b36092fa",
+    "bytes_per_launch": 1073873408 + 3436032,
+    "pairs_per_launch": 32,
+    "capture": "the timed launch itself (first launch in the headline_timed NVTX range, "
+               "32 pairs, 456 CTAs of 160 threads)",
 }
 # the workload both arms measure (the reference arm times a bounded sample)
 WORKLOAD = ("paper-scale pairs N=2048 N_T=64 FP32, LISI+augLISI in one pass, distinct "
@@ -149,7 +151,11 @@ def profiled_traffic(pairs_per_launch):
         return None
     if h.hexdigest() != PROFILED_TRAFFIC["sha256"]:
         return None
-    return int(round(PROFILED_TRAFFIC["bytes_per_pair"] * pairs_per_launch))
+    if pairs_per_launch == PROFILED_TRAFFIC["pairs_per_launch"]:
+        return PROFILED_TRAFFIC["bytes_per_launch"]
+    # another batch size: scaled by pairs (traffic grows in proportion)
+    return int(round(PROFILED_TRAFFIC["bytes_per_launch"] * pairs_per_launch /
+                     PROFILED_TRAFFIC["pairs_per_launch"]))
 
 
 def measured_peak():
@@ -342,7 +348,19 @@ def _pool_pairs(rank, count):
     return [synth.paper_pair(pair_index=rank * count + i) for i in range(count)]
 
 
-def _time_plan(iqa, ctx, plan, stream, K, warmup):
+def _nvtx(name):
+    """An NVTX range around a timed region (a profiler can select the timed
+    launches by it); a no-op where NVTX is unavailable."""
+    import contextlib
+    try:
+        import torch
+        return torch.cuda.nvtx.range(name)
+    except Exception:
+        return contextlib.nullcontext()
+
+
+def _time_plan(iqa, ctx, plan, stream, K, warmup, label=None):
+    import contextlib
     import torch
     with torch.cuda.stream(stream):
         for _ in range(max(3, warmup)):
@@ -350,7 +368,7 @@ def _time_plan(iqa, ctx, plan, stream, K, warmup):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
+    with torch.cuda.stream(stream), (_nvtx(label) if label else contextlib.nullcontext()):
         e0.record(stream)
         for _ in range(K):
             iqa.iqa_plan_launch(plan, stream)
@@ -473,7 +491,7 @@ def precision_report(iqa, ctx, params, stream, batch=16):
                 for _ in range(B)]
         pairs = [iqa.make_pair(xs[i], ys[i], N, NT, *outs[i]) for i in range(B)]
         plan = iqa.iqa_plan_create(ctx, pairs, code, params, iqa.IQA_PLAN_GRAPH)
-        ms = _time_plan(iqa, ctx, plan, stream, 20, 3)
+        ms = _time_plan(iqa, ctx, plan, stream, 20, 3, label="precision_" + name)
         iqa.iqa_plan_destroy(plan)
         es = 4 if name == "f32" else 2
         out[name] = {
@@ -620,11 +638,14 @@ def serving_report(iqa, ctx, seconds, rate=2000.0, n_refs=32, seed=4):
         trace.append(iqa.make_request(rid, int(rng.choice([32, 64, 128])), 10**9 + i,
                                       drop, add))
 
-    def run(dtype, one_pair, timed, burst=None):
+    def run(dtype, one_pair, timed, burst=None, marks=0):
+        # steps of up to 32 pairs and 1 GB of input (a mean request is about
+        # 239 MB in FP16): at saturation a step batches several requests
         srv = iqa.iqa_server_create(ctx, dtype=dtype, max_pairs_per_step=32,
                                     max_inflight_steps=4, pool_bytes=8 << 30,
                                     one_pair_per_launch=one_pair,
-                                    max_step_bytes=256 << 20, params=PARAMS)
+                                    max_step_bytes=1 << 30, params=PARAMS,
+                                    time_kernels=marks)
         try:
             for rid, cat in cats.items():
                 iqa.iqa_server_add_reference(srv, rid, cat, 7 + rid)
@@ -651,6 +672,17 @@ def serving_report(iqa, ctx, seconds, rate=2000.0, n_refs=32, seed=4):
         "served_saturation": run(iqa.IQA_F16, 0, False, burst),
         "baseline_saturation": run(iqa.IQA_F32, 1, False, burst),
     }
+    # the same bursts again with timing marks around every step's two kernels
+    # (the marks cut the launch overlap between them, so they stay out of the
+    # runs above): device time per pair of the epoch generator and of the map
+    # kernel, as they ran concurrently in up to four steps
+    split = {}
+    for name, dt, one in (("served", iqa.IQA_F16, 0), ("baseline", iqa.IQA_F32, 1)):
+        r = run(dt, one, False, burst, marks=1)
+        split[name] = {k: r[k] for k in ("pairs_per_s", "mean_pairs_per_step",
+                                          "generator_ms_per_pair", "map_ms_per_pair",
+                                          "mean_step_generator_ms", "mean_step_map_ms")}
+    out["saturation_device_split"] = split
     return out
 
 
@@ -706,10 +738,40 @@ def run_ours(args):
     clocks.start()
     K = max(1, args.steps)
     barrier(world)
-    dev_ms = _time_plan(iqa, ctx, plan, stream, K, args.warmup)
+    dev_ms = _time_plan(iqa, ctx, plan, stream, K, args.warmup, label="headline_timed")
     barrier(world)
     clk = clocks.stop()
     t_max_ms = max_over_ranks(dev_ms, world, dev)
+    # end to end through the host-buffer entry point: one call per step over
+    # the same B pairs in page-locked host memory, uploads pipelined with the
+    # reductions, maps read back (measured right after the headline, before
+    # the other reports fill host and device memory)
+    hx = [torch.from_numpy(x).pin_memory() for x, _ in host_pairs]
+    hy = [torch.from_numpy(y).pin_memory() for _, y in host_pairs]
+    hl = [np.empty(T * T, np.float32) for _ in range(B)]
+    ha = [np.empty(T * T, np.float32) for _ in range(B)]
+    hpairs = [iqa.make_host_pair(hx[i], hy[i], N, NT, hl[i], ha[i]) for i in range(B)]
+    iqa.iqa_both_host_many(ctx, hpairs, iqa.IQA_F32, params)
+    barrier(world)
+    t0 = time.perf_counter()
+    E = max(1, args.e2e_steps)
+    for i in range(E):
+        iqa.iqa_both_host_many(ctx, hpairs, iqa.IQA_F32, params)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    assert all(np.all(np.isfinite(v)) for v in hl + ha)
+    # context for e2e: plain page-locked host -> device copies of the same
+    # host buffers (one pair per repetition)
+    scratch = torch.empty(N * N, device=dev)
+    scratch.copy_(hx[0].view(-1), non_blocking=True)
+    torch.cuda.synchronize()
+    c0 = time.perf_counter()
+    for r in range(10):
+        scratch.copy_(hx[r % B].view(-1), non_blocking=True)
+        scratch.copy_(hy[r % B].view(-1), non_blocking=True)
+    torch.cuda.synchronize()
+    h2d_gbs = 10 * pair_bytes / (time.perf_counter() - c0) / 1e9
+    del scratch
+
     KG = max(10, min(K, 2000))
     other = {}
     for name, flags in (("stream_ordered", 0), ("graph", iqa.IQA_PLAN_GRAPH)):
@@ -824,12 +886,26 @@ def run_ours(args):
         K16 = max(10, min(K, 2000))
         ms = _time_plan(iqa, ctx, pl16, stream, K16, 3)
         iqa.iqa_plan_destroy(pl16)
+        # twice the pairs per launch (a second copy of each), so that a launch
+        # moves the same bytes as the FP32 step: separates the per-launch cost
+        # from the per-byte cost of the 16-bit kernel
+        hx2 = hx16 + [t.clone() for t in hx16]
+        hy2 = hy16 + [t.clone() for t in hy16]
+        l2 = [torch.empty(T * T, device=dev) for _ in range(2 * B)]
+        a2 = [torch.empty(T * T, device=dev) for _ in range(2 * B)]
+        pl2 = iqa.iqa_plan_create(ctx, [iqa.make_pair(hx2[i], hy2[i], N, NT, l2[i], a2[i])
+                                        for i in range(2 * B)], code, params,
+                                  iqa.IQA_PLAN_INDEPENDENT)
+        ms2 = _time_plan(iqa, ctx, pl2, stream, K16, 3)
+        iqa.iqa_plan_destroy(pl2)
         storage16[name] = {
             "GBs": round(K16 * B * pair_bytes / 2 / (ms * 1e-3) / 1e9, 1),
             "pixel_pairs_per_s": round(K16 * B * N * N / (ms * 1e-3), 1),
             "us_per_pair": round(ms * 1e3 / (K16 * B), 3),
-            "tuned": tuned16}
-        del hx16, hy16
+            "tuned": tuned16,
+            "GBs_%d_pairs_per_launch" % (2 * B): round(K16 * 2 * B * pair_bytes / 2 /
+                                                       (ms2 * 1e-3) / 1e9, 1)}
+        del hx16, hy16, hx2, hy2, l2, a2
 
     prec, prec_maps = None, None
     if rank == 0 and world == 1 and not args.no_precision:
@@ -887,33 +963,6 @@ def run_ours(args):
     serve = None
     if rank == 0 and world == 1 and args.serve_seconds > 0:
         serve = serving_report(iqa, ctx, args.serve_seconds)
-
-    # end to end through the host-buffer entry point: one call per step over
-    # the same B pairs in page-locked host memory, uploads pipelined with the
-    # reductions, maps read back
-    hx = [torch.from_numpy(x).pin_memory() for x, _ in host_pairs]
-    hy = [torch.from_numpy(y).pin_memory() for _, y in host_pairs]
-    hl = [np.empty(T * T, np.float32) for _ in range(B)]
-    ha = [np.empty(T * T, np.float32) for _ in range(B)]
-    hpairs = [iqa.make_host_pair(hx[i], hy[i], N, NT, hl[i], ha[i]) for i in range(B)]
-    iqa.iqa_both_host_many(ctx, hpairs, iqa.IQA_F32, params)
-    barrier(world)
-    t0 = time.perf_counter()
-    E = max(1, args.e2e_steps)
-    for i in range(E):
-        iqa.iqa_both_host_many(ctx, hpairs, iqa.IQA_F32, params)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
-    assert all(np.all(np.isfinite(v)) for v in hl + ha)
-    # context for e2e: a plain page-locked host -> device copy of one pair
-    scratch = torch.empty(2 * N * N, device=dev)
-    hcat = torch.cat([hx[0].view(-1), hy[0].view(-1)]).pin_memory()
-    scratch.copy_(hcat, non_blocking=True)
-    torch.cuda.synchronize()
-    c0 = time.perf_counter()
-    for _ in range(10):
-        scratch.copy_(hcat, non_blocking=True)
-    torch.cuda.synchronize()
-    h2d_gbs = 10 * pair_bytes / (time.perf_counter() - c0) / 1e9
 
     total_bytes = sum_over_ranks(K * B * pair_bytes, world, dev)
     value = total_bytes / (t_max_ms * 1e-3) / 1e9
@@ -997,7 +1046,10 @@ def run_ours(args):
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": profiled_traffic(B),
                          "algorithmic_bytes": B * pair_bytes,
-                         "traffic_source": "ncu, %s" % PROFILED_TRAFFIC["capture"],
+                         "traffic_source": "ncu, %s%s" % (
+                             PROFILED_TRAFFIC["capture"],
+                             "" if B == PROFILED_TRAFFIC["pairs_per_launch"] else
+                             ", scaled by pairs to %d" % B),
                          "peak_source": peak_src,
                          "kernel": "iqa_stream_kernel<float,%d,1,1> (persistent, TMA)"
                                    % info["config"]["threads"]},
