@@ -63,7 +63,10 @@ struct StreamParams {
     int npairs;
     int stage_bytes;         // bytes of ONE image per stage
     int stages;
-    int pad_;
+    // units of every CTA's first grab, taken statically (CTA b takes units
+    // [b * head_units, (b + 1) * head_units)); dynamic grabs then count from
+    // gridDim.x * head_units.  0 or 1 = one unit; only with a work counter.
+    int head_units;
     long long total_units;
     int *status;             // error word (nullable), nonzero = failed
     long long timeout_ns;    // bound on every wait
@@ -75,7 +78,7 @@ struct StreamParams {
     unsigned long long *sched;
     int inject_stall;        // test hook: 1 = the producer issues nothing
     // 1: the launch does not depend on the kernel before it in the stream
-    // (an independent plan): each CTA's first unit is copied before waiting
+    // (an independent plan): each CTA's first grab is copied before waiting
     // for that kernel, and only the shared counter waits for it
     int overlap_head;
     // nullable: {npairs, total_units} in device memory, read at launch in
@@ -254,17 +257,20 @@ __global__ void __launch_bounds__(CT + 32, 1)
         // atomicAdd on the shared counter per grab, issued one grab ahead so
         // that its latency hides behind the current grab's copies.  A grab
         // spans about kGrabBytes of each image (several small units, or one).
-        // The first unit of every CTA is its own index (no atomic on the
-        // launch's critical path); dynamic grabs then count from gridDim.x,
-        // and shrink toward one unit as the work runs out (guided), so that
-        // the CTAs finish close together.
+        // The first grab of every CTA is static: head units from its own
+        // index times head (no atomic on the launch's critical path; head > 1
+        // makes a grab of small units about as many bytes as one large unit);
+        // dynamic grabs then count from gridDim.x * head, and shrink toward
+        // one unit as the work runs out (guided), so that the CTAs finish
+        // close together.
         constexpr uint32_t kGrabBytes = 65536;
-        long long u = blockIdx.x, u_end = u + 1, nxt = -1, nxt_end = -1, i = 0;
+        const long long head = (sp.sched && sp.head_units > 1) ? sp.head_units : 1;
+        long long u = blockIdx.x * head, u_end = u + head, nxt = -1, nxt_end = -1, i = 0;
         bool have_next = false;
         // A kernel earlier in the stream (programmatic dependent launch) may
         // still be running: wait for it before any work is fetched or copied.
         // An independent launch (sp.overlap_head) instead issues its first
-        // unit's copies at once, overlapping that kernel's drain, and waits
+        // grab's copies at once, overlapping that kernel's drain, and waits
         // before it touches the shared counter, which that kernel may still
         // be using (and so that this grid never completes before it).
         bool waited = sp.overlap_head == 0;
@@ -283,7 +289,7 @@ __global__ void __launch_bounds__(CT + 32, 1)
                     const unsigned share = left > 0 ? (unsigned)left / (unsigned)span : 0u;
                     g = share > 1 ? share : 1u;
                 }
-                nxt = (long long)gridDim.x +
+                nxt = (long long)gridDim.x * head +
                       (long long)atomicAdd(&sp.sched[0], (unsigned long long)g);
                 nxt_end = nxt + g;
             } else {
@@ -385,8 +391,8 @@ __global__ void __launch_bounds__(CT + 32, 1)
                     pph ^= 1u;
                 }
             }
-            if (!waited) {
-                // the first unit is in flight (independent launch)
+            if (!waited && (last || u + 1 >= u_end)) {
+                // the first grab is in flight (independent launch)
                 asm volatile("griddepcontrol.wait;" ::: "memory");
                 waited = true;
                 if (!last && ok) fetch_next(bytes * (uint32_t)d.chunks);

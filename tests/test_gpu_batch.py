@@ -248,3 +248,48 @@ def test_plan_rejects_unknown_flags(ctx):
     with pytest.raises(iqa.IqaError) as ei:
         iqa.iqa_plan_create(ctx, b.pairs(), iqa.IQA_F32, PARAMS, 4)
     assert ei.value.status == iqa.IQA_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("dt,code", [("f32", 0), ("f16", 1)])
+def test_small_unit_plans_static_first_grab(ctx, orc, dt, code):
+    """Plans of N_T = 16 pairs, whose units are small (16-32 KB per image): each
+    CTA's static first grab then spans several units (about 64 KB per image),
+    and dynamic grabs count from the grid size times that.  Independent plans
+    back to back into NaN-filled maps, and a one-pair plan with fewer units
+    than the grid's first grabs: every map written, bit-identical to a
+    stream-ordered plan, which matches the oracle."""
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    specs = [(512, 16), (1024, 16), (256, 16), (768, 16)]
+    ref = Batch(specs, dtype=dt, seed=41)
+    _run(ctx, ref, flags=0, dtype_code=code)
+    want = [ref.results(i) for i in range(len(specs))]
+    for i, (N, NT) in enumerate(specs):
+        x, y = ref.host[i]
+        parity.assert_parity(want[i], parity.oracle_maps(orc, x, y, NT, PARAMS), PARAMS)
+    outs = [Batch.__new__(Batch) for _ in range(4)]
+    plans = []
+    try:
+        for o in outs:
+            o.specs, o.host, o.dev = ref.specs, ref.host, ref.dev
+            o.out = [tuple(torch.full_like(t, float("nan")) for t in ref.out[i])
+                     for i in range(len(specs))]
+            plans.append(iqa.iqa_plan_create(ctx, o.pairs(), code, PARAMS,
+                                             iqa.IQA_PLAN_INDEPENDENT))
+        st = torch.cuda.current_stream()
+        for _ in range(3):
+            for p in plans:
+                iqa.iqa_plan_launch(p, st)
+        iqa.iqa_wait(ctx, st, 20_000_000)
+    finally:
+        for p in plans:
+            iqa.iqa_plan_destroy(p)
+    for o in outs:
+        for i in range(len(specs)):
+            for u, v in zip(o.results(i), want[i]):
+                assert np.array_equal(u, v)
+    # one N=256 pair: 16 units of 16 tiles, fewer than the grid's first grabs
+    one = Batch([(256, 16)], dtype=dt, seed=42)
+    _run(ctx, one, flags=iqa.IQA_PLAN_INDEPENDENT, dtype_code=code, launches=3)
+    x, y = one.host[0]
+    parity.assert_parity(one.results(0), parity.oracle_maps(orc, x, y, 16, PARAMS), PARAMS)
