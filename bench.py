@@ -46,7 +46,8 @@ PAPER_NT_SWEEP = (16, 32, 64, 128, 256)
 PAPER_N_SWEEP = (512, 1024, 2048, 4096, 8192)
 
 # DRAM traffic of the timed kernel from one ncu capture of the timed launch
-# itself (summary and command in profiles/iqa_stream_kernel_N2048_NT64_batch32_f32.md):
+# itself (its summary and command are under profiles/, named for this kernel
+# and workload):
 # dram__bytes_read.sum + dram__bytes_write.sum of the first launch inside the
 # headline_timed NVTX range, 32 pairs.  Valid only for the kernel sources it was
 # taken on: `traffic` is reported as null when their hash no longer matches.
@@ -89,7 +90,7 @@ def parse_args(argv=None):
                     help="length of the served Poisson trace (0: skip serving)")
     ap.add_argument("--precision-batch", type=int, default=16,
                     help="N=8192 pairs per launch in the precision throughput report")
-    ap.add_argument("--tune-iters", type=int, default=3,
+    ap.add_argument("--tune-iters", type=int, default=10,
                     help="launches per autotuner candidate (0: keep the default shape)")
     return ap.parse_args(argv)
 
@@ -464,7 +465,7 @@ def small_pair_report(iqa, ctx, params, stream):
                       am[0].cpu().numpy().astype(np.float64))}
 
 
-def precision_report(iqa, ctx, params, stream, batch=16):
+def precision_report(iqa, ctx, params, stream, batch=16, tune_iters=3):
     """The precision workload's size (N=8192, N_T=64, point + extended sources,
     1e4 dynamic range, sigma 5e-3) stored as FP32, FP16 and BF16: the batched
     throughput of each storage type, and pair 0's maps from those launches
@@ -491,6 +492,9 @@ def precision_report(iqa, ctx, params, stream, batch=16):
                 for _ in range(B)]
         pairs = [iqa.make_pair(xs[i], ys[i], N, NT, *outs[i]) for i in range(B)]
         plan = iqa.iqa_plan_create(ctx, pairs, code, params, iqa.IQA_PLAN_GRAPH)
+        if tune_iters > 0:
+            out.setdefault("tuned", {})[name] = iqa.iqa_plan_autotune(plan, stream,
+                                                                      tune_iters).as_dict()
         ms = _time_plan(iqa, ctx, plan, stream, 20, 3, label="precision_" + name)
         iqa.iqa_plan_destroy(plan)
         es = 4 if name == "f32" else 2
@@ -909,7 +913,8 @@ def run_ours(args):
 
     prec, prec_maps = None, None
     if rank == 0 and world == 1 and not args.no_precision:
-        prec, prec_maps = precision_report(iqa, ctx, params, stream, args.precision_batch)
+        prec, prec_maps = precision_report(iqa, ctx, params, stream, args.precision_batch,
+                                           min(args.tune_iters, 3))
 
     # N sweep at N_T = 64 (the paper's other Fig. 1 axis), about the same bytes
     # per launch at every N, built on the device from the step's pairs:

@@ -65,7 +65,10 @@ static iqa_status check_pair(iqa_ctx *ctx, const iqa_pair &p, iqa_dtype dtype, i
 // launch streams while the previous launch drains.  Measured on GB300 (32
 // N=2048 pairs per launch, same box, alternated): 256 KB against 64 KB gives
 // FP16 N_T = 16 / 64 +2.6% / +3.4% and FP32 about the same; 512 KB loses 4%
-// on FP32 N_T = 32 and 64 (the static grabs then unbalance the CTAs).
+// on FP32 N_T = 32 and 64 (the static grabs then unbalance the CTAs).  512 KB
+// for 16-bit storage only, with the static grabs capped at a quarter of the
+// work, measured within +-0.8% of this at N = 1024 ... 8192 (autotuned, two
+// runs alternated), so one size is kept.
 constexpr long long kHeadBytes = 262144;
 
 // (Re)build the descriptor table for cfg and upload it.
