@@ -55,8 +55,8 @@ PROFILED_TRAFFIC = {
     "sources": ["paper_2501_10653_gb300/csrc/iqa_device.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream_f32.cu"],
-    "sha256": "5a26356ce9ee19ea1e4da53b6a39774b55dc01b4ad79ad9810befdb7b36092fa",
-    "bytes_per_launch": 1073873408 + 3436032,
+    "sha256": "c8c508fcdd95cb09a94166a79c7675f0350b2ec3b3691f435d5f15054cbf0814",
+    "bytes_per_launch": 1073862400 + 3398656,
     "pairs_per_launch": 32,
     "capture": "the timed launch itself (first launch in the headline_timed NVTX range, "
                "32 pairs, 456 CTAs of 160 threads)",
@@ -811,6 +811,28 @@ def run_ours(args):
         p1.record(stream)
     torch.cuda.synchronize()
     per_pair_us = p0.elapsed_time(p1) * 1e3 / (reps * G)
+    # the same calls as independent calls (IQA_OPT_INDEPENDENT_CALLS: each one
+    # loads and reduces its pixels while the call before it drains; every call
+    # writes its own maps, so the promise holds), captured and replayed alike
+    iqa.iqa_set_option(ctx, iqa.IQA_OPT_INDEPENDENT_CALLS, 1)
+    try:
+        gi = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gi, stream=stream):
+            for i in range(G):
+                j = i % B
+                iqa.iqa_both(ctx, dx[j], dy[j], iqa.IQA_F32, N, NT, params, lisi[j], aug[j],
+                             None, stream)
+    finally:
+        iqa.iqa_set_option(ctx, iqa.IQA_OPT_INDEPENDENT_CALLS, 0)
+    with torch.cuda.stream(stream):
+        gi.replay()
+        p0.record(stream)
+        for _ in range(reps):
+            gi.replay()
+        p1.record(stream)
+    torch.cuda.synchronize()
+    indep_call_us = p0.elapsed_time(p1) * 1e3 / (reps * G)
+    del gi
     # one pair per launch through the plan API instead: B one-pair independent
     # plans launched directly back to back (each launch's first units stream
     # while the previous one drains)
@@ -1024,6 +1046,8 @@ def run_ours(args):
                 "lisi_only_single_us_median10": round(float(np.median(lisi_only)), 3),
                 "auglisi_only_single_us_median10": round(float(np.median(aug_only)), 3),
                 "launch": plain_cfg,
+                "independent_calls_us_per_pair": round(indep_call_us, 3),
+                "independent_calls_GBs": round(pair_bytes / (indep_call_us * 1e-6) / 1e9, 1),
                 "independent_plans_us_per_pair": round(plan_pair_us, 3),
                 "independent_plans_GBs": round(pair_bytes / (plan_pair_us * 1e-6) / 1e9, 1),
                 "timing": "back-to-back iqa_both launches replayed from a CUDA graph; "

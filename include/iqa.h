@@ -314,8 +314,9 @@ typedef struct iqa_plan iqa_plan;
  * with the values this launch writes.  The plan's own previous launch
  * qualifies (a plan's results repeat bit for bit), and so does another
  * plan's launch over other outputs.  Each CTA then starts copying its first
- * unit while that kernel drains, instead of after it completes; every other
- * access, and the launch's completion, still follow it.  Breaking the
+ * grab (about 256 KB of each image) while that kernel drains, instead of
+ * after it completes; every other access, and the launch's completion, still
+ * follow it.  Breaking the
  * promise gives wrong maps, not a fault.  Effective for direct launches (a
  * graph replay waits for the previous work anyway). */
 #define IQA_PLAN_INDEPENDENT 2
@@ -586,7 +587,19 @@ typedef enum {
     /* Fault injection for tests of the failure path: 1 makes the producer warp
      * of the persistent kernels issue no copies, so every consumer wait runs
      * out; 0 (default) is normal operation. */
-    IQA_OPT_INJECT_STALL = 2
+    IQA_OPT_INJECT_STALL = 2,
+    /* 1: the caller promises, for every later iqa_lisi / iqa_auglisi /
+     * iqa_both call on this context that runs the streaming-load kernel, the
+     * same as IQA_PLAN_INDEPENDENT does for a plan: the kernel just before the
+     * call on the stream does not write the call's images, does not read its
+     * maps or sums, and writes them, if at all, only with the values this
+     * call writes (a stream of calls over other outputs, or the same call
+     * repeated, qualifies).  Each CTA then loads and reduces its pixels while
+     * that kernel drains, and waits for it only before writing its maps, so
+     * the call's writes and completion still follow it.  Breaking the promise
+     * gives wrong maps, not a fault.  0 (default): every CTA waits before its
+     * first access. */
+    IQA_OPT_INDEPENDENT_CALLS = 3
 } iqa_option;
 
 /*

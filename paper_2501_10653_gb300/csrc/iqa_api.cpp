@@ -327,6 +327,7 @@ TileArgs make_args(const void *x, const void *y, int N, int NT,
     a.lisi = lisi;
     a.aug = aug;
     a.sums = sums;
+    a.overlap = 0;
     return a;
 }
 
@@ -368,6 +369,7 @@ static iqa_status run_maps(iqa_ctx *ctx, const void *x, const void *y,
         return run_stream_pair(ctx, x, y, dtype, N, NT, c, P, lisi, aug, sums, maps,
                                (cudaStream_t)stream);
     TileArgs a = make_args(x, y, N, NT, c, P, lisi, aug, sums);
+    a.overlap = ctx->independent_calls;
     cudaError_t e = launch_tiles(a, c, dtype, maps, N / NT, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tile kernel launch");
     return IQA_OK;
@@ -573,6 +575,13 @@ iqa_status iqa_set_option(iqa_ctx *ctx, int option, long long value)
             return IQA_ERR_INVALID_ARG;
         }
         ctx->inject_stall = (int)value;
+        return IQA_OK;
+    case IQA_OPT_INDEPENDENT_CALLS:
+        if (value != 0 && value != 1) {
+            set_error(ctx, "independent-calls takes 0 or 1");
+            return IQA_ERR_INVALID_ARG;
+        }
+        ctx->independent_calls = (int)value;
         return IQA_OK;
     default:
         set_error(ctx, "unknown option %d", option);

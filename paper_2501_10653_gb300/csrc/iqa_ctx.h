@@ -23,6 +23,7 @@ struct iqa_ctx {
     int *d_status = nullptr;
     long long wait_timeout_ns = 1000000000LL;
     int inject_stall = 0;  // test hook, see IQA_OPT_INJECT_STALL
+    int independent_calls = 0;  // see IQA_OPT_INDEPENDENT_CALLS
 
     std::mutex err_mu;
     std::string last_error;

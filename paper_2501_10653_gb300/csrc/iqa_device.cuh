@@ -75,6 +75,10 @@ struct TileArgs {
     float *lisi;        // (T*T) map or nullptr
     float *aug;         // (T*T) map or nullptr
     double *sums;       // (T*T*4) or nullptr
+    int overlap;        // 1: an independent call (the kernel before it in the
+                        // stream writes none of these images and touches none
+                        // of the outputs): wait for that kernel only before
+                        // writing; 0: wait before any access
 };
 
 // ---------------------------------------------------------------------------

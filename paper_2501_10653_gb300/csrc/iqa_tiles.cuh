@@ -17,7 +17,7 @@ namespace iqa {
 
 namespace cg = cooperative_groups;
 
-template <typename T, int VEC, int ILP, int THREADS, bool DO_A, bool DO_B>
+template <typename T, int VEC, int ILP, int THREADS, bool DO_A, bool DO_B, bool OVERLAP>
 __global__ void __launch_bounds__(THREADS)
     iqa_tiles_kernel(const TileArgs p)
 {
@@ -26,9 +26,11 @@ __global__ void __launch_bounds__(THREADS)
 
     // programmatic dependent launch: let the next kernel in the stream be
     // scheduled as this grid drains, and wait for the previous one (which may
-    // have written these images or maps) before the first access
+    // have written these images or maps) before the first access -- or, for
+    // an independent call (OVERLAP), only before the first write, so the
+    // loads stream while that kernel drains
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if constexpr (!OVERLAP) asm volatile("griddepcontrol.wait;" ::: "memory");
 
     const int tile_col0 = blockIdx.x * p.TX;
     const int srank = blockIdx.y % p.S;
@@ -45,6 +47,7 @@ __global__ void __launch_bounds__(THREADS)
         accumulate_unit<T, VEC, ILP, THREADS, DO_A, DO_B>(xu, yu, p.N, p.RH, p.LPU,
                                                           p.C1f, acc);
     reduce_unit<THREADS>(acc, p.TX, p.LPU, p.LPT, red, part, CtaBarrier());
+    if constexpr (OVERLAP) asm volatile("griddepcontrol.wait;" ::: "memory");
 
     const long long t0 = (long long)tile_row * p.T + tile_col0;
     const bool out_ok = IQA_CHECK(t0 + p.TX <= (long long)p.T * p.T && p.TX <= kMaxTX);
@@ -73,13 +76,15 @@ __global__ void __launch_bounds__(THREADS)
 }
 
 // Launches the kernel, or, with occ non-null, stores the number of its CTAs
-// that fit one SM at once (no launch).
-template <typename T, int VEC, int ILP, int THREADS, bool DO_A, bool DO_B>
+// that fit one SM at once (no launch).  An independent call (p.overlap) runs
+// the OVERLAP instantiation, which only the 16-byte vector paths have; the
+// stream-ordered kernels compile exactly as they would without it.
+template <typename T, int VEC, int ILP, int THREADS, bool DO_A, bool DO_B, bool OVERLAP>
 static cudaError_t launch_one(const TileArgs &p, int rows, cudaStream_t st, int *occ)
 {
     if (occ)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            occ, iqa_tiles_kernel<T, VEC, ILP, THREADS, DO_A, DO_B>, THREADS, 0);
+            occ, iqa_tiles_kernel<T, VEC, ILP, THREADS, DO_A, DO_B, OVERLAP>, THREADS, 0);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(p.T / p.TX), (unsigned)(rows * p.S), 1);
     cfg.blockDim = dim3(THREADS, 1, 1);
@@ -97,17 +102,25 @@ static cudaError_t launch_one(const TileArgs &p, int rows, cudaStream_t st, int 
         attr[1].val.clusterDim.z = 1;
         cfg.numAttrs = 2;
     }
-    return cudaLaunchKernelEx(&cfg, iqa_tiles_kernel<T, VEC, ILP, THREADS, DO_A, DO_B>, p);
+    return cudaLaunchKernelEx(&cfg, iqa_tiles_kernel<T, VEC, ILP, THREADS, DO_A, DO_B, OVERLAP>,
+                              p);
+}
+
+template <typename T, int VEC, int ILP, int THREADS, bool OVERLAP>
+static cudaError_t by_maps_o(const TileArgs &p, int maps, int rows, cudaStream_t st, int *occ)
+{
+    switch (maps) {
+    case MAPS_A: return launch_one<T, VEC, ILP, THREADS, true, false, OVERLAP>(p, rows, st, occ);
+    case MAPS_B: return launch_one<T, VEC, ILP, THREADS, false, true, OVERLAP>(p, rows, st, occ);
+    default: return launch_one<T, VEC, ILP, THREADS, true, true, OVERLAP>(p, rows, st, occ);
+    }
 }
 
 template <typename T, int VEC, int ILP, int THREADS>
 static cudaError_t by_maps(const TileArgs &p, int maps, int rows, cudaStream_t st, int *occ)
 {
-    switch (maps) {
-    case MAPS_A: return launch_one<T, VEC, ILP, THREADS, true, false>(p, rows, st, occ);
-    case MAPS_B: return launch_one<T, VEC, ILP, THREADS, false, true>(p, rows, st, occ);
-    default: return launch_one<T, VEC, ILP, THREADS, true, true>(p, rows, st, occ);
-    }
+    if (VEC > 1 && p.overlap) return by_maps_o<T, VEC, ILP, THREADS, true>(p, maps, rows, st, occ);
+    return by_maps_o<T, VEC, ILP, THREADS, false>(p, maps, rows, st, occ);
 }
 
 template <typename T, int VEC, int ILP>

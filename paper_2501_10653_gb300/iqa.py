@@ -141,6 +141,7 @@ IQA_PLAN_INDEPENDENT = 2
 IQA_NOALLOC_MAX_PAIRS = 64
 IQA_OPT_WAIT_TIMEOUT_US = 1
 IQA_OPT_INJECT_STALL = 2
+IQA_OPT_INDEPENDENT_CALLS = 3
 
 _lib = None
 _vp = ctypes.c_void_p

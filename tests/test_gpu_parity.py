@@ -601,3 +601,45 @@ def test_auglisi_localises_dropped_sources(ctx, paper):
     import test_paper_behaviour as pb
     l, a, _ = parity.gpu_maps(ctx, paper[0], paper[1], pb.NT, PARAMS)
     pb.check_localisation(l, a)
+
+
+def test_independent_calls_back_to_back(ctx, orc):
+    """IQA_OPT_INDEPENDENT_CALLS: each one-pair call loads and reduces its
+    pixels while the kernel before it drains, and waits for that kernel only
+    before writing.  Calls over distinct pairs (one-tile units, two-tile
+    units, 256-thread CTAs and a cluster-split tile), back to back three
+    times into NaN-filled maps: every map written, bit-identical to the same
+    calls stream-ordered, which match the oracle."""
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    specs = [(1024, 64), (2048, 64), (2048, 128), (512, 256), (1024, 32)]
+    pairs = [synth.paper_pair(pair_index=i, N=N) for i, (N, _) in enumerate(specs)]
+    dev = [(parity.to_device(x), parity.to_device(y)) for x, y in pairs]
+
+    def outputs():
+        return [(torch.full(((N // NT) ** 2,), float("nan"), device="cuda"),
+                 torch.full(((N // NT) ** 2,), float("nan"), device="cuda"),
+                 torch.full(((N // NT) ** 2, 4), float("nan"), device="cuda",
+                            dtype=torch.float64)) for N, NT in specs]
+
+    def run_all(outs, rounds):
+        st = torch.cuda.current_stream()
+        for _ in range(rounds):
+            for (N, NT), (dx, dy), o in zip(specs, dev, outs):
+                iqa.iqa_both(ctx, dx, dy, iqa.IQA_F32, N, NT, PARAMS, o[0], o[1], o[2], st)
+        torch.cuda.synchronize()
+        return [tuple(t.cpu().numpy() for t in o) for o in outs]
+
+    want = run_all(outputs(), 1)
+    for (N, NT), (x, y), w in zip(specs, pairs, want):
+        parity.assert_parity(w, parity.oracle_maps(orc, x, y, NT, PARAMS), PARAMS)
+    iqa.iqa_set_option(ctx, iqa.IQA_OPT_INDEPENDENT_CALLS, 1)
+    try:
+        got = run_all(outputs(), 3)
+    finally:
+        iqa.iqa_set_option(ctx, iqa.IQA_OPT_INDEPENDENT_CALLS, 0)
+    for g, w in zip(got, want):
+        for u, v in zip(g, w):
+            assert np.array_equal(u, v)
+    with pytest.raises(iqa.IqaError):
+        iqa.iqa_set_option(ctx, iqa.IQA_OPT_INDEPENDENT_CALLS, 2)
