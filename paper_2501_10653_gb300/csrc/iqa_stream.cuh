@@ -3,10 +3,11 @@
 // Same method as iqa_tiles.cuh (arxiv 2501.10653, Section 2, Eq. 1 and Eq. 2:
 // clamp, tile, four per-tile sums, per-tile ratios), laid out for GB300:
 //   * one CTA per SM slot loops over units (TX whole tiles across x N_T rows,
-//     up to 1024 elements wide) of one or many image pairs: its own index
-//     first, then grabs of consecutive units from a global counter (about
-//     64 KB per image each, fetched one grab ahead, shrinking toward one unit
-//     as the work runs out), or round-robin without a counter; the producer
+//     up to 1024 elements wide) of one or many image pairs: a static first
+//     grab of consecutive units from its own index (head_units of them), then
+//     grabs of consecutive units from a global counter (about 64 KB per image
+//     each, fetched one grab ahead, shrinking toward one unit as the work runs
+//     out), or round-robin without a counter; the producer
 //     tells the consumers which pair a stage holds and the first tile of its
 //     unit through per-stage slots in shared memory;
 //   * a producer warp streams every unit in chunks of CH rows with TMA tensor

@@ -150,6 +150,16 @@ def test_bad_requests_and_config(lib):
         iqa.iqa_server_create(None, max_pairs_per_step=65, simulate=1)
     with pytest.raises(iqa.IqaError):
         iqa.iqa_server_create(None, simulate=0)
+    for bad in (dict(max_inflight_steps=9), dict(generator_blocks_per_sm=9),
+                dict(generator_blocks_per_sm=-1), dict(map_ctas_per_sm=5),
+                dict(time_kernels=2)):
+        with pytest.raises(iqa.IqaError) as ei:
+            iqa.iqa_server_create(None, simulate=1, **bad)
+        assert ei.value.status == iqa.IQA_ERR_INVALID_ARG, bad
+    # the new settings at their limits are accepted
+    ok = iqa.iqa_server_create(None, simulate=1, max_inflight_steps=8,
+                               generator_blocks_per_sm=8, map_ctas_per_sm=1, time_kernels=1)
+    iqa.iqa_server_destroy(ok)
 
 
 def test_step_byte_cap_splits_large_from_small(lib):
