@@ -64,12 +64,12 @@ static iqa_status check_pair(iqa_ctx *ctx, const iqa_pair &p, iqa_dtype dtype, i
 // Bytes of each image in every CTA's static first grab: what an independent
 // launch streams while the previous launch drains.  Measured on GB300 (32
 // N=2048 pairs per launch, same box, alternated): 256 KB against 64 KB gives
-// FP16 N_T = 16 / 64 +2.6% / +3.4% and FP32 about the same; 512 KB loses 4%
-// on FP32 N_T = 32 and 64 (the static grabs then unbalance the CTAs).  512 KB
-// for 16-bit storage only, with the static grabs capped at a quarter of the
-// work, measured within +-0.8% of this at N = 1024 ... 8192 (autotuned, two
-// runs alternated), so one size is kept.
-constexpr long long kHeadBytes = 262144;
+// FP16 N_T = 16 / 64 +2.6% / +3.4% and FP32 about the same; 512 KB gives FP16
+// N_T = 32 / 64 a further +1% but loses 4% on FP32 N_T = 32 and 64 (the
+// static grabs then unbalance the CTAs), so 16-bit storage takes 512 KB.
+// (Capping the static grabs at a quarter of the work instead cost FP16 up to
+// 0.8% at N = 1024 ... 4096.)
+static long long head_bytes(iqa_dtype dtype) { return elem_size(dtype) == 2 ? 524288 : 262144; }
 
 // (Re)build the descriptor table for cfg and upload it.
 static iqa_status plan_build(iqa_plan *pl, const TileConfig &cfg)
@@ -98,15 +98,16 @@ static iqa_status plan_build(iqa_plan *pl, const TileConfig &cfg)
     pl->cfg = cfg;
     pl->total_units = units;
     pl->grid = stream_grid(ctx, cfg, units);
-    // each CTA's first grab spans about kHeadBytes of each image (at most 8
-    // units), counted on the first pair's units (the largest); one unit of
-    // 16K-32K pixel pairs alone is 32-64 KB
+    // each CTA's first grab spans about head_bytes() of each image (at most
+    // 8 units), counted on the first pair's units (the largest); one unit of
+    // 16K-32K pixel pairs alone is 32-128 KB
     if (n > 0) {
         const PairDesc &d0 = pl->h_table[0];
         const long long unit_bytes =
             (long long)d0.TX * d0.NT * d0.NT * elem_size(pl->dtype);
         pl->head_units = (int)std::max<long long>(
-            1, std::min<long long>(8, kHeadBytes / std::max<long long>(1, unit_bytes)));
+            1, std::min<long long>(8, head_bytes(pl->dtype) /
+                                          std::max<long long>(1, unit_bytes)));
     }
     return IQA_OK;
 }
