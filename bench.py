@@ -756,24 +756,34 @@ def run_ours(args):
     ha = [np.empty(T * T, np.float32) for _ in range(B)]
     hpairs = [iqa.make_host_pair(hx[i], hy[i], N, NT, hl[i], ha[i]) for i in range(B)]
     iqa.iqa_both_host_many(ctx, hpairs, iqa.IQA_F32, params)
-    barrier(world)
-    t0 = time.perf_counter()
-    E = max(1, args.e2e_steps)
-    for i in range(E):
-        iqa.iqa_both_host_many(ctx, hpairs, iqa.IQA_F32, params)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
-    assert all(np.all(np.isfinite(v)) for v in hl + ha)
     # context for e2e: plain page-locked host -> device copies of the same
-    # host buffers (one pair per repetition)
+    # host buffers (one pair per repetition), before and after it
     scratch = torch.empty(N * N, device=dev)
-    scratch.copy_(hx[0].view(-1), non_blocking=True)
-    torch.cuda.synchronize()
-    c0 = time.perf_counter()
-    for r in range(10):
-        scratch.copy_(hx[r % B].view(-1), non_blocking=True)
-        scratch.copy_(hy[r % B].view(-1), non_blocking=True)
-    torch.cuda.synchronize()
-    h2d_gbs = 10 * pair_bytes / (time.perf_counter() - c0) / 1e9
+
+    def plain_h2d():
+        scratch.copy_(hx[0].view(-1), non_blocking=True)
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        for r in range(10):
+            scratch.copy_(hx[r % B].view(-1), non_blocking=True)
+            scratch.copy_(hy[r % B].view(-1), non_blocking=True)
+        torch.cuda.synchronize()
+        return 10 * pair_bytes / (time.perf_counter() - c0) / 1e9
+
+    h2d_before = plain_h2d()
+    # three blocks of E steps; the median block is reported (the host link is
+    # shared with the machine's other GPUs, so one block can catch a transient)
+    E = max(1, args.e2e_steps)
+    blocks = []
+    for _ in range(3):
+        barrier(world)
+        t0 = time.perf_counter()
+        for i in range(E):
+            iqa.iqa_both_host_many(ctx, hpairs, iqa.IQA_F32, params)
+        blocks.append(max_over_ranks(time.perf_counter() - t0, world, dev))
+    e2e_s = float(np.median(blocks))
+    assert all(np.all(np.isfinite(v)) for v in hl + ha)
+    h2d_gbs = max(h2d_before, plain_h2d())
     del scratch
 
     KG = max(10, min(K, 2000))
@@ -996,7 +1006,8 @@ def run_ours(args):
     peak, peak_src = measured_peak()
     per_launch_us = dev_ms * 1e3 / K
     achieved = B * pair_bytes / (per_launch_us * 1e-6) / 1e9
-    e2e_value = sum_over_ranks(E * B * pair_bytes, world, dev) / e2e_s / 1e9
+    e2e_bytes = sum_over_ranks(E * B * pair_bytes, world, dev)
+    e2e_value = e2e_bytes / e2e_s / 1e9
 
     result = None
     if rank == 0:
@@ -1069,6 +1080,8 @@ def run_ours(args):
                     "ms_per_step": round(e2e_s * 1e3 / E, 4),
                     "api": "iqa_both_host_many over the step's %d pairs, page-locked "
                            "host buffers, uploads pipelined with reductions" % B,
+                    "timing": "median of 3 blocks of %d steps" % E,
+                    "blocks_GBs": [round(e2e_bytes / b / 1e9, 1) for b in blocks],
                     "plain_h2d_copy_GBs": round(h2d_gbs, 1)},
             "gpu_launches": K,
             "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
