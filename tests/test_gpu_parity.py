@@ -603,7 +603,8 @@ def test_auglisi_localises_dropped_sources(ctx, paper):
     pb.check_localisation(l, a)
 
 
-def test_independent_calls_back_to_back(ctx, orc):
+@pytest.mark.parametrize("dt", ["f32", "f16"])
+def test_independent_calls_back_to_back(ctx, orc, dt):
     """IQA_OPT_INDEPENDENT_CALLS: each one-pair call loads and reduces its
     pixels while the kernel before it drains, and waits for that kernel only
     before writing.  Calls over distinct pairs (one-tile units, two-tile
@@ -613,7 +614,7 @@ def test_independent_calls_back_to_back(ctx, orc):
     import torch
     from paper_2501_10653_gb300 import iqa
     specs = [(1024, 64), (2048, 64), (2048, 128), (512, 256), (1024, 32)]
-    pairs = [synth.paper_pair(pair_index=i, N=N) for i, (N, _) in enumerate(specs)]
+    pairs = [synth.paper_pair(pair_index=i, N=N, dtype=dt) for i, (N, _) in enumerate(specs)]
     dev = [(parity.to_device(x), parity.to_device(y)) for x, y in pairs]
 
     def outputs():
@@ -626,7 +627,8 @@ def test_independent_calls_back_to_back(ctx, orc):
         st = torch.cuda.current_stream()
         for _ in range(rounds):
             for (N, NT), (dx, dy), o in zip(specs, dev, outs):
-                iqa.iqa_both(ctx, dx, dy, iqa.IQA_F32, N, NT, PARAMS, o[0], o[1], o[2], st)
+                iqa.iqa_both(ctx, dx, dy, parity.dtype_code(pairs[0][0]), N, NT, PARAMS, o[0],
+                             o[1], o[2], st)
         torch.cuda.synchronize()
         return [tuple(t.cpu().numpy() for t in o) for o in outs]
 
