@@ -224,8 +224,11 @@ iqa_status iqa_both_host_many(iqa_ctx *ctx, const iqa_host_pair *pairs, int npai
  * them.  Needs 16-byte aligned images, NT a multiple of 16 bytes, and
  * tiles_across * NT <= 256, or 512 or 1024 with N a multiple of 256.
  *   threads        128, 256 or 512 consumer threads (plus one producer warp)
- *   tiles_across   whole tiles per unit (plans choose it per pair from
- *                  unit_kpx: the widest unit of at most unit_kpx K pixels)
+ *   tiles_across   whole tiles per unit (one pair: as given, one tile row
+ *                  down; plans choose the unit per pair from unit_kpx: the
+ *                  widest unit of at most unit_kpx K pixel pairs, then as many
+ *                  tile rows down as still fit and divide N/NT, when the unit
+ *                  row is reduced by the segmented shuffle tree)
  *   stages         2..16;   stage_kb  2, 4, 8 or 16;   ctas_per_sm  1..4
  * maps: 1 = LISI only, 2 = augLISI only, 3 = both (also used when sums are
  * requested).  Unused fields are ignored.
@@ -359,6 +362,16 @@ typedef struct {
 } iqa_plan_stats;
 
 iqa_status iqa_plan_info(const iqa_plan *plan, iqa_plan_stats *out);
+
+/*
+ * Sets the plan's launch shape (variant 1: threads, stages, stage_kb,
+ * ctas_per_sm, unit_kpx in 1..1024; the per-pair unit follows from unit_kpx),
+ * rebuilds its descriptors and re-captures its graph.  Synchronous; no launch
+ * of the plan may be running.  On error the plan keeps its previous shape.
+ * Errors: IQA_ERR_INVALID_ARG (not variant 1, unit_kpx out of range, or a
+ * shape some pair of the plan cannot take), IQA_ERR_CUDA.
+ */
+iqa_status iqa_plan_set_config(iqa_plan *plan, const iqa_launch_config *cfg);
 
 /*
  * Autotuner: times the plan under several launch shapes of the persistent

@@ -81,8 +81,7 @@ static iqa_status plan_build(iqa_plan *pl, const TileConfig &cfg)
     for (int i = 0; i < n; ++i) {
         const iqa_pair &p = pl->pairs[i];
         TileConfig c = cfg;
-        c.TX = stream_tiles_across(p.N, p.NT, pl->dtype, cfg.threads,
-                                   (long long)cfg.unit_kpx * 1024);
+        stream_unit_shape(c, p.N, p.NT, pl->dtype);
         if (!stream_config_valid(p.N, p.NT, pl->dtype, c, &why)) {
             set_error(ctx, "pair %d (N=%d NT=%d): %s", i, p.N, p.NT, why.c_str());
             return IQA_ERR_INVALID_ARG;
@@ -104,7 +103,7 @@ static iqa_status plan_build(iqa_plan *pl, const TileConfig &cfg)
     if (n > 0) {
         const PairDesc &d0 = pl->h_table[0];
         const long long unit_bytes =
-            (long long)d0.TX * d0.NT * d0.NT * elem_size(pl->dtype);
+            (long long)d0.RH * d0.TX * d0.NT * d0.NT * elem_size(pl->dtype);
         pl->head_units = (int)std::max<long long>(
             1, std::min<long long>(8, head_bytes(pl->dtype) /
                                           std::max<long long>(1, unit_bytes)));
@@ -313,6 +312,40 @@ iqa_status iqa_plan_info(const iqa_plan *plan, iqa_plan_stats *out)
     out->config.ctas_per_sm = plan->cfg.ctas_per_sm;
     out->config.unit_kpx = plan->cfg.unit_kpx;
     return IQA_OK;
+}
+
+iqa_status iqa_plan_set_config(iqa_plan *plan, const iqa_launch_config *cfg)
+{
+    if (!plan) return IQA_ERR_INVALID_ARG;
+    iqa_ctx *ctx = plan->ctx;
+    if (!cfg || cfg->variant != 1 || cfg->unit_kpx < 1 || cfg->unit_kpx > 1024) {
+        set_error(ctx, "a plan takes a variant 1 shape with unit_kpx in 1..1024");
+        return IQA_ERR_INVALID_ARG;
+    }
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+    const TileConfig keep = plan->cfg;
+    TileConfig c = keep;
+    c.threads = cfg->threads;
+    c.stages = cfg->stages;
+    c.stage_kb = cfg->stage_kb;
+    c.ctas_per_sm = cfg->ctas_per_sm;
+    c.unit_kpx = cfg->unit_kpx;
+    iqa_status s = plan_build(plan, c);
+    if (s != IQA_OK) {
+        // the plan keeps its previous shape (and the error message this one set)
+        std::string msg;
+        {
+            std::lock_guard<std::mutex> g(ctx->err_mu);
+            msg = ctx->last_error;
+        }
+        plan_build(plan, keep);
+        set_error(ctx, "%s", msg.c_str());
+    }
+    if (s == IQA_OK && plan->exec) s = plan_capture(plan);
+    cudaSetDevice(prev);
+    return s;
 }
 
 iqa_status iqa_plan_autotune(iqa_plan *plan, iqa_stream stream, int iters,

@@ -74,6 +74,8 @@ bool stream_config_valid(int N, int NT, iqa_dtype dtype, const TileConfig &c,
 TileConfig default_stream_config(int N, int NT, iqa_dtype dtype);
 int unit_boxes(int N, int BW);
 int stream_tiles_across(int N, int NT, iqa_dtype dtype, int threads, long long unit_px);
+int stream_unit_rows(int N, int NT, iqa_dtype dtype, int threads, int TX, long long unit_px);
+void stream_unit_shape(TileConfig &c, int N, int NT, iqa_dtype dtype);
 iqa_status fill_pair_desc(iqa_ctx *ctx, PairDesc *d, const void *x, const void *y, int N,
                           int NT, iqa_dtype dtype, const TileConfig &c, const iqa_params &P,
                           float *lisi, float *aug, double *sums, long long unit_begin);

@@ -376,7 +376,50 @@ template <int ID, int COUNT> struct NamedBarrier {
     }
 };
 
-__device__ __forceinline__ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+__host__ __device__ __forceinline__ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Whether a unit of TX > 1 tiles across, LPU vectors per unit row and LPT per
+// tile row takes the segmented shuffle tree of reduce_unit (LPT a power of two
+// up to 32, and whole unit rows per warp or whole warps per unit row).
+__host__ __device__ __forceinline__ bool segmented_reduce(int TX, int LPU, int LPT)
+{
+    return TX > 1 && is_pow2(LPT) && LPT <= 32 && (LPU >= 32 || is_pow2(LPU));
+}
+
+// Reduction slots of one tile row in the segmented form: one per (group of
+// threads that covers a unit row, tile), (THREADS / max(LPU, 32)) * TX.
+__host__ __device__ __forceinline__ int segmented_slots(int threads, int TX, int LPU)
+{
+    return threads / (LPU >= 32 ? LPU : 32) * TX;
+}
+
+// Segmented shuffle tree of one tile row (segmented_reduce() holds): each
+// tile's LPT lanes are summed (and, when a warp spans several unit rows, the
+// same columns of those rows), and the lane heading each segment stores the
+// partial of its (row group, tile) in red[k][slot0 + group * TX + tile].
+template <int THREADS>
+__device__ __forceinline__ void segmented_partials(const float (&acc)[4], int TX, int LPU,
+                                                   int LPT, int slot0, float (*red)[THREADS])
+{
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    float v[4] = {acc[0], acc[1], acc[2], acc[3]};
+    for (int o = 1; o < LPT; o <<= 1) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+    for (int o = LPU; o < 32; o <<= 1) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+    const int span = LPU >= 32 ? LPU : 32;  // threads per row group
+    const int col = tid % LPU;
+    if (col % LPT == 0 && (LPU >= 32 || lane < LPU)) {
+        const int slot = slot0 + (tid / span) * TX + col / LPT;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) red[k][slot] = v[k];
+    }
+}
 
 // Cross-thread reduction of one unit, in FP32 (the low-rate FP64 pipe of this
 // GPU is kept off the per-unit path).  part[tl * 4 + k] receives tile tl's sum
@@ -416,24 +459,9 @@ __device__ __forceinline__ void reduce_unit(const float (&acc)[4], int TX, int L
         bar();
         return;
     }
-    if (is_pow2(LPT) && LPT <= 32 && (LPU >= 32 || is_pow2(LPU))) {
-        float v[4] = {acc[0], acc[1], acc[2], acc[3]};
-        for (int o = 1; o < LPT; o <<= 1) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-        }
-        for (int o = LPU; o < 32; o <<= 1) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-        }
-        const int span = LPU >= 32 ? LPU : 32;  // threads per row group
-        const int groups = THREADS / span;
-        const int col = tid % LPU;
-        if (col % LPT == 0 && (LPU >= 32 || lane < LPU)) {
-            const int slot = (tid / span) * TX + col / LPT;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) red[k][slot] = v[k];
-        }
+    if (segmented_reduce(TX, LPU, LPT)) {
+        segmented_partials<THREADS>(acc, TX, LPU, LPT, 0, red);
+        const int groups = THREADS / (LPU >= 32 ? LPU : 32);
         bar();
         for (int tl = tid; tl < TX; tl += THREADS) {
             float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};

@@ -18,6 +18,7 @@ struct TileConfig {
     int ilp = 4;        // 2, 4 or 8 vectors of each image in flight per thread
     int vec = 0;        // elements per load: the full 16-byte vector, or 1
     int TX = 1;         // whole tiles across a unit
+    int RH = 1;         // variant 1: tile rows down a unit
     int S = 1;          // CTAs per tile (cluster along y), 1..8
     int stages = 8;
     int stage_kb = 8;

@@ -161,8 +161,7 @@ extern "C" iqa_status iqa_batch_noalloc(const iqa_pair *pairs, int npairs, iqa_d
     for (int k = 0; k < npairs; ++k) {
         const iqa_pair &p = pairs[order[k]];
         TileConfig c = cfg;
-        c.TX = stream_tiles_across(p.N, p.NT, dtype, cfg.threads,
-                                   (long long)cfg.unit_kpx * 1024);
+        stream_unit_shape(c, p.N, p.NT, dtype);
         std::string why;
         if (!stream_config_valid(p.N, p.NT, dtype, c, &why)) {
             set_error(nullptr, "pair %d: %s", order[k], why.c_str());

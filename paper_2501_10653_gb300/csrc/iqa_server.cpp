@@ -400,8 +400,7 @@ iqa_status launch_step(iqa_server *srv, Slot &s)
         o += 2 * (size_t)r.T * r.T;
         if (srv->cfg.one_pair_per_launch) continue;
         TileConfig c = srv->kcfg;
-        c.TX = stream_tiles_across(r.N, r.r.NT, srv->cfg.dtype, c.threads,
-                                   (long long)c.unit_kpx * 1024);
+        stream_unit_shape(c, r.N, r.r.NT, srv->cfg.dtype);
         iqa_status st = fill_pair_desc(ctx, &s.h_pairs[k], ref.d_image, epoch, r.N, r.r.NT,
                                        srv->cfg.dtype, c, srv->P, dl, da, nullptr, units);
         if (st != IQA_OK) return st;

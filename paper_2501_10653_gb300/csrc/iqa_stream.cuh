@@ -2,8 +2,8 @@
 //
 // Same method as iqa_tiles.cuh (arxiv 2501.10653, Section 2, Eq. 1 and Eq. 2:
 // clamp, tile, four per-tile sums, per-tile ratios), laid out for GB300:
-//   * one CTA per SM slot loops over units (TX whole tiles across x N_T rows,
-//     up to 1024 elements wide) of one or many image pairs: a static first
+//   * one CTA per SM slot loops over units (TX whole tiles across, up to 1024
+//     elements wide, x RH tile rows down) of one or many image pairs: a static first
 //     grab of consecutive units from its own index (head_units of them), then
 //     grabs of consecutive units from a global counter (about 64 KB per image
 //     each, fetched one grab ahead, shrinking toward one unit as the work runs
@@ -15,9 +15,12 @@
 //     segments for rows wider than 256) of x and y into a ring of shared-
 //     memory stages, signalling completion on per-stage mbarriers;
 //   * consumer warps read each stage with 16-byte shared loads, clamp, form
-//     the terms, accumulate in registers across the unit's chunks, release the
-//     stage, and reduce the unit (shuffle trees, a named barrier) while the
-//     producer is already a stage ahead;
+//     the terms, accumulate in registers across a tile row's chunks and
+//     release the stage; at the end of each tile row a segmented shuffle tree
+//     leaves per-warp partials in shared memory, and at the end of the unit one
+//     named barrier lets each thread sum and write one tile, while the
+//     producer is already a stage ahead (units of several tile rows take the
+//     per-unit work once for all of them);
 //   * launches use programmatic dependent launch: the next kernel in the
 //     stream may be scheduled while this one drains, and the producer waits
 //     for the previous grid before it fetches work or issues a copy;
@@ -46,9 +49,11 @@ struct PairDesc {
     long long unit_begin;    // first global unit index of this pair
     int N, NT, T;            // image side, tile side, tiles per row
     int TX;                  // tiles across a unit
-    int units_x;             // units per tile row = T / TX
+    int RH;                  // tile rows down a unit (T % RH == 0)
+    int units_x;             // units per band of RH tile rows = T / TX
     int CH;                  // rows per chunk
-    int chunks;              // chunks per unit = NT / CH
+    int CPR;                 // chunks per tile row = NT / CH
+    int chunks;              // chunks per unit = RH * CPR
     int LPU;                 // 16-byte vectors per unit row = TX * NT / VEC
     int LPT;                 // vectors per tile row = NT / VEC
     int NB;                  // 256-element boxes across a unit row: 1 = 2-D map
@@ -335,12 +340,12 @@ __global__ void __launch_bounds__(CT + 32, 1)
                 const long long lu = u - d.unit_begin;
                 // a 32-bit division whenever the unit index fits (every pair
                 // below 2^31 units): the 64-bit one is a long subroutine
-                const int trow = lu <= (long long)INT_MAX ? (int)lu / d.units_x
+                const int band = lu <= (long long)INT_MAX ? (int)lu / d.units_x
                                                           : (int)(lu / d.units_x);
-                const int ucol = (int)(lu - (long long)trow * d.units_x);
+                const int ucol = (int)(lu - (long long)band * d.units_x);
                 col0 = ucol * d.TX * d.NT;
-                row0 = trow * d.NT;
-                t0 = (long long)trow * d.T + (long long)ucol * d.TX;
+                row0 = band * d.RH * d.NT;
+                t0 = (long long)band * d.RH * d.T + (long long)ucol * d.TX;
                 bytes = (uint32_t)(d.CH * d.TX * d.NT * (int)sizeof(T));
                 if (!have_next && waited) fetch_next(bytes * (uint32_t)d.chunks);
             }
@@ -366,7 +371,8 @@ __global__ void __launch_bounds__(CT + 32, 1)
                 }
                 // the chunk's box lies inside the image and fits one stage
                 // (checked build only; a violation stops the CTA like an abort)
-                if (!IQA_CHECK(pi < npairs && u - d.unit_begin < (long long)d.T * d.units_x &&
+                if (!IQA_CHECK(pi < npairs && d.RH >= 1 && d.T % d.RH == 0 &&
+                               u - d.unit_begin < (long long)(d.T / d.RH) * d.units_x &&
                                col0 >= 0 && col0 + d.TX * d.NT <= d.N &&
                                (col0 * (int)sizeof(T)) % 16 == 0 &&
                                (d.NB == 1 || col0 % 256 == 0) &&
@@ -435,6 +441,11 @@ __global__ void __launch_bounds__(CT + 32, 1)
     const PairDesc *d = nullptr;
     long long t0 = -1;  // first tile of the current unit within its pair
     int c = 0, V = 0, chunks = 0;
+    // chunks per tile row, chunk within the current tile row, that row's
+    // index within the unit; seg: the unit takes the segmented reduction, one
+    // block of reduction slots per tile row (units of several tile rows)
+    int cpr = 0, cr = 0, r = 0, spr = 0;
+    bool seg = false;
     float C1f = 0.0f;
     Kahan ka, kb, kx, ky;
     // ring position of chunk k: stage s = k % S, full-barrier parity
@@ -456,6 +467,11 @@ __global__ void __launch_bounds__(CT + 32, 1)
             d = &descs[stage_pair[s]];
             V = d->CH * d->LPU;
             chunks = d->chunks;
+            cpr = d->CPR;
+            seg = segmented_reduce(d->TX, d->LPU, d->LPT);
+            spr = segmented_slots(CT, d->TX, d->LPU);
+            cr = 0;
+            r = 0;
             C1f = d->C1f;
             ka = Kahan();
             kb = Kahan();
@@ -508,12 +524,51 @@ __global__ void __launch_bounds__(CT + 32, 1)
         if (DO_B) kb.add(p.b.x + p.b.y);
         kx.add(p.x.x + p.x.y);
         ky.add(p.y.x + p.y.y);
-        if (++c == chunks) {
+        ++c;
+        if (seg) {
+            if (++cr == cpr) {
+                // tile row r of the unit is complete: this warp's partials of
+                // its tiles go to the row's block of reduction slots (no
+                // barrier: the blocks of a unit's rows are disjoint, and every
+                // read of the previous unit's slots precedes the named barrier
+                // 2 that began this unit)
+                cr = 0;
+                const float acc[4] = {ka.value(), kb.value(), kx.value(), ky.value()};
+                if (IQA_CHECK((r + 1) * spr <= CT))
+                    segmented_partials<CT>(acc, d->TX, d->LPU, d->LPT, r * spr, red);
+                ka = Kahan();
+                kb = Kahan();
+                kx = Kahan();
+                ky = Kahan();
+                ++r;
+            }
+            if (c == chunks) {
+                // the unit's RH x TX tiles: thread tl sums tile tl's row-group
+                // partials in order and writes it
+                c = 0;
+                named_bar(1, CT);
+                const int TX = d->TX, T = d->T, RH = d->RH;
+                const int groups = spr / TX;
+                const bool out_ok = IQA_CHECK(t0 + (long long)(RH - 1) * T + TX <=
+                                              (long long)T * T && RH * spr <= CT);
+                for (int tl = tid; tl < RH * TX && out_ok; tl += CT) {
+                    const int rr = tl / TX, tx = tl - rr * TX;
+                    float sm[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                    for (int g = 0; g < groups; ++g) {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) sm[k] += red[k][rr * spr + g * TX + tx];
+                    }
+                    write_tile_desc(*d, t0 + (long long)rr * T + tx, sm[0], sm[1], sm[2],
+                                    sm[3]);
+                }
+            }
+        } else if (c == chunks) {
             c = 0;
             const int TX = d->TX, LPU = d->LPU, LPT = d->LPT;
             float acc[4] = {ka.value(), kb.value(), kx.value(), ky.value()};
             reduce_unit<CT>(acc, TX, LPU, LPT, red, part, NamedBarrier<1, CT>());
-            const bool out_ok = IQA_CHECK(t0 + TX <= (long long)d->T * d->T && TX <= kMaxTX);
+            const bool out_ok = IQA_CHECK(t0 + TX <= (long long)d->T * d->T && TX <= kMaxTX &&
+                                          d->RH == 1);
             for (int tl = tid; tl < TX && out_ok; tl += CT)
                 write_tile_desc(*d, t0 + tl, part[tl * 4 + 0], part[tl * 4 + 1],
                                 part[tl * 4 + 2], part[tl * 4 + 3]);

@@ -78,6 +78,11 @@ bool stream_config_valid(int N, int NT, iqa_dtype dtype, const TileConfig &c,
                     "with N a multiple of 256, for the TMA kernel");
     const int LPU = BW / V;
     if (c.TX > 1 && c.threads % LPU) return fail("threads must be a multiple of the unit row");
+    if (c.RH < 1 || T % c.RH) return fail("tile rows per unit must divide N/NT");
+    if (c.RH > 1 && !segmented_reduce(c.TX, LPU, NT / V))
+        return fail("several tile rows per unit need the segmented reduction");
+    if (c.RH > 1 && c.RH * segmented_slots(c.threads, c.TX, LPU) > c.threads)
+        return fail("too many tile rows per unit for the reduction slots");
     if (!chunk_rows(NT, BW, es, c.stage_kb * 1024))
         return fail("a unit row does not fit one stage");
     if ((stream_smem_bytes(c.stages, c.stage_kb * 1024, c.threads) + 1024) * c.ctas_per_sm >
@@ -111,6 +116,30 @@ int stream_tiles_across(int N, int NT, iqa_dtype dtype, int threads, long long u
         best = tx;
     }
     return best;
+}
+
+// Most tile rows down a unit of TX tiles across (dividing N / NT) whose
+// pixel pairs stay within unit_px and whose per-row reduction slots fit the
+// consumer threads; 1 where the unit does not take the segmented reduction.
+int stream_unit_rows(int N, int NT, iqa_dtype dtype, int threads, int TX, long long unit_px)
+{
+    const int V = 16 / elem_size(dtype);
+    const int T = N / NT, LPU = TX * NT / V, LPT = NT / V;
+    if (!segmented_reduce(TX, LPU, LPT)) return 1;
+    const int spr = segmented_slots(threads, TX, LPU);
+    int best = 1;
+    for (int rh = 2; rh * spr <= threads && (long long)rh * TX * NT * NT <= unit_px; ++rh)
+        if (T % rh == 0) best = rh;
+    return best;
+}
+
+// The unit of a batched launch: as wide as stream_tiles_across() allows, then
+// as many tile rows down as stream_unit_rows() allows, for c.unit_kpx.
+void stream_unit_shape(TileConfig &c, int N, int NT, iqa_dtype dtype)
+{
+    const long long unit_px = (long long)c.unit_kpx * 1024;
+    c.TX = stream_tiles_across(N, NT, dtype, c.threads, unit_px);
+    c.RH = stream_unit_rows(N, NT, dtype, c.threads, c.TX, unit_px);
 }
 
 TileConfig default_stream_config(int N, int NT, iqa_dtype dtype)
@@ -187,9 +216,11 @@ iqa_status fill_pair_desc(iqa_ctx *ctx, PairDesc *d, const void *x, const void *
     d->NT = NT;
     d->T = N / NT;
     d->TX = c.TX;
+    d->RH = c.RH;
     d->units_x = d->T / c.TX;
     d->CH = CH;
-    d->chunks = NT / CH;
+    d->CPR = NT / CH;
+    d->chunks = c.RH * (NT / CH);
     d->LPU = BW / V;
     d->LPT = NT / V;
     d->NB = NB;
@@ -204,7 +235,7 @@ iqa_status fill_pair_desc(iqa_ctx *ctx, PairDesc *d, const void *x, const void *
 long long pair_units(int N, int NT, const TileConfig &c)
 {
     const long long T = N / NT;
-    return T * (T / c.TX);
+    return (T / c.RH) * (T / c.TX);
 }
 
 int stream_grid(iqa_ctx *ctx, const TileConfig &c, long long units)

@@ -172,6 +172,7 @@ def _declare(lib):
         "iqa_plan_destroy": ([_vp], None),
         "iqa_plan_info": ([_vp, P(iqa_plan_stats)], _st),
         "iqa_plan_autotune": ([_vp, _vp, _i, P(iqa_launch_config)], _st),
+        "iqa_plan_set_config": ([_vp, P(iqa_launch_config)], _st),
         "iqa_batch_noalloc": ([P(iqa_pair), _i, _i, P(iqa_params), _vp], _st),
         "iqa_merge": ([_vp, _vp, _i, _i, P(iqa_params), _vp, _vp, _vp, _vp], _st),
         "iqa_both_host_many": ([_vp, P(iqa_host_pair), _i, _i, P(iqa_params)], _st),
@@ -371,6 +372,17 @@ def iqa_plan_info(plan):
     st = iqa_plan_stats()
     _check(plan.ctx, lib().iqa_plan_info(plan.handle, ctypes.byref(st)))
     return st
+
+
+def iqa_plan_set_config(plan, cfg):
+    """Variant 1 shape for the plan (an iqa_launch_config, or a dict of its
+    fields: threads, stages, stage_kb, ctas_per_sm, unit_kpx)."""
+    if isinstance(cfg, dict):
+        full = {"variant": 1, "threads": 128, "ilp": 0, "tiles_across": 0, "split": 1,
+                "vector": 1, "stages": 2, "stage_kb": 16, "ctas_per_sm": 3, "unit_kpx": 16}
+        full.update(cfg)
+        cfg = iqa_launch_config(**full)
+    _check(plan.ctx, lib().iqa_plan_set_config(plan.handle, ctypes.byref(cfg)))
 
 
 def iqa_plan_autotune(plan, stream=None, iters=5):

@@ -91,6 +91,26 @@ def main():
         torch.cuda.synchronize()
     _violations("batched plans and no-alloc batches")
 
+    # batched plans whose units span several tile rows (explicit shapes)
+    for N, NT, dt, th, kpx in ((1024, 16, "f32", 128, 32), (288, 16, "f32", 128, 32),
+                               (2048, 32, "f32", 256, 64), (768, 16, "f16", 128, 32),
+                               (512, 8, "f32", 128, 64)):
+        x, y = synth.mixed_batch_pair(1, N, dtype=dt)
+        dx, dy = parity.to_device(x), parity.to_device(y)
+        T = N // NT
+        o = (torch.empty(T * T, device="cuda"), torch.empty(T * T, device="cuda"),
+             torch.empty((T * T, 4), dtype=torch.float64, device="cuda"))
+        plan = iqa.iqa_plan_create(ctx, [iqa.make_pair(dx, dy, N, NT, *o)],
+                                   parity.dtype_code(x), PARAMS, iqa.IQA_PLAN_INDEPENDENT)
+        iqa.iqa_plan_set_config(plan, {"threads": th, "unit_kpx": kpx})
+        for _ in range(2):
+            iqa.iqa_plan_launch(plan, st)
+        torch.cuda.synchronize()
+        iqa.iqa_plan_destroy(plan)
+        parity.assert_parity(tuple(t.cpu().numpy() for t in o),
+                             parity.oracle_maps(orc, x, y, NT, PARAMS), PARAMS)
+    _violations("plans of several tile rows per unit")
+
     # Eq. 3 / Eq. 4 merge: thread, warp and cluster shapes
     x, y = synth.paper_pair(N=1024)
     _, _, sums = parity.gpu_maps(ctx, x, y, 8, PARAMS)

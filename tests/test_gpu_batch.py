@@ -252,9 +252,9 @@ def test_plan_rejects_unknown_flags(ctx):
 
 @pytest.mark.parametrize("dt,code", [("f32", 0), ("f16", 1)])
 def test_small_unit_plans_static_first_grab(ctx, orc, dt, code):
-    """Plans of N_T = 16 pairs, whose units are small (16-32 KB per image): each
-    CTA's static first grab then spans several units (about 64 KB per image),
-    and dynamic grabs count from the grid size times that.  Independent plans
+    """Plans of N_T = 16 pairs, whose units (several tile rows of at most 32
+    tiles) hold 32-64 KB of each image: each CTA's static first grab then spans
+    several units, and dynamic grabs count from the grid size times that.  Independent plans
     back to back into NaN-filled maps, and a one-pair plan with fewer units
     than the grid's first grabs: every map written, bit-identical to a
     stream-ordered plan, which matches the oracle."""
@@ -288,8 +288,98 @@ def test_small_unit_plans_static_first_grab(ctx, orc, dt, code):
         for i in range(len(specs)):
             for u, v in zip(o.results(i), want[i]):
                 assert np.array_equal(u, v)
-    # one N=256 pair: 16 units of 16 tiles, fewer than the grid's first grabs
+    # one N=256 pair: a few units, fewer than the grid's first grabs
     one = Batch([(256, 16)], dtype=dt, seed=42)
     _run(ctx, one, flags=iqa.IQA_PLAN_INDEPENDENT, dtype_code=code, launches=3)
     x, y = one.host[0]
     parity.assert_parity(one.results(0), parity.oracle_maps(orc, x, y, 16, PARAMS), PARAMS)
+
+
+def _plan_with_shape(ctx, batch, shape, flags=0, dtype_code=0, launches=1):
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    plan = iqa.iqa_plan_create(ctx, batch.pairs(), dtype_code, PARAMS, flags)
+    try:
+        iqa.iqa_plan_set_config(plan, shape)
+        for t in batch.out:
+            for u in t:
+                u.fill_(float("nan"))
+        for _ in range(launches):
+            iqa.iqa_plan_launch(plan, torch.cuda.current_stream())
+        iqa.iqa_wait(ctx, torch.cuda.current_stream(), 20_000_000)
+        info = iqa.iqa_plan_info(plan)
+    finally:
+        iqa.iqa_plan_destroy(plan)
+    return info
+
+
+# (N, N_T, storage, threads, unit_kpx, tiles across TX, tile rows per unit RH):
+# a unit of RH > 1 tile rows keeps per-tile-row partials and reduces them at
+# its end.  Cases: RH 1 / 2 / 4 at the same TX (128-vector unit rows); RH 9 on
+# 8-vector unit rows (a warp spans four unit rows); 3-D boxes (1024-element
+# unit rows); 16-bit storage.
+MULTI_ROW = [
+    (1024, 16, "f32", 128, 8, 32, 1),
+    (1024, 16, "f32", 128, 16, 32, 2),
+    (1024, 16, "f32", 128, 32, 32, 4),
+    (288, 16, "f32", 128, 32, 2, 9),
+    (2048, 32, "f32", 256, 64, 32, 2),
+    (768, 16, "f16", 128, 32, 16, 2),
+    (512, 8, "f32", 128, 64, 64, 2),
+]
+
+
+@pytest.mark.parametrize("N,NT,dt,threads,kpx,TX,RH", MULTI_ROW)
+def test_multi_row_units_against_oracle(ctx, orc, N, NT, dt, threads, kpx, TX, RH):
+    """Units of several tile rows: the plan's work list has (N/NT/RH) *
+    (N/NT/TX) units, and every tile (maps and exported sums) matches the
+    oracle."""
+    b = Batch([(N, NT)], dtype=dt, seed=51)
+    code = {"f32": 0, "f16": 1, "bf16": 2}[dt]
+    info = _plan_with_shape(ctx, b, {"threads": threads, "unit_kpx": kpx}, dtype_code=code)
+    T = N // NT
+    assert info.total_units == (T // RH) * (T // TX)
+    assert info.config.unit_kpx == kpx and info.config.threads == threads
+    x, y = b.host[0]
+    parity.assert_parity(b.results(0), parity.oracle_maps(orc, x, y, NT, PARAMS), PARAMS)
+
+
+def test_multi_row_units_change_no_bit(ctx):
+    """At the same unit width a thread sums the same columns of the same chunks
+    whatever the tile rows per unit, so 1, 2 and 4 rows give the same bits,
+    stream-ordered and as independent launches back to back."""
+    from paper_2501_10653_gb300 import iqa
+    b = Batch([(1024, 16), (512, 16)], seed=52)
+    _plan_with_shape(ctx, b, {"unit_kpx": 8})
+    want = [b.results(i) for i in range(2)]
+    for kpx in (16, 32):
+        for flags, launches in ((0, 1), (iqa.IQA_PLAN_INDEPENDENT | iqa.IQA_PLAN_GRAPH, 3)):
+            _plan_with_shape(ctx, b, {"unit_kpx": kpx}, flags=flags, launches=launches)
+            for i in range(2):
+                for u, v in zip(b.results(i), want[i]):
+                    assert np.array_equal(u, v), (kpx, flags, i)
+
+
+def test_plan_set_config_rejects_and_keeps_shape(ctx):
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    b = Batch([(512, 16)], seed=53)
+    plan = iqa.iqa_plan_create(ctx, b.pairs(), 0, PARAMS, iqa.IQA_PLAN_GRAPH)
+    try:
+        iqa.iqa_plan_set_config(plan, {"unit_kpx": 16})
+        before = iqa.iqa_plan_info(plan)
+        for bad in ({"unit_kpx": 0}, {"unit_kpx": 2048}, {"variant": 0},
+                    {"stages": 1}, {"threads": 96}, {"stage_kb": 32},
+                    {"stages": 16, "stage_kb": 16}):
+            with pytest.raises(iqa.IqaError) as ei:
+                iqa.iqa_plan_set_config(plan, bad)
+            assert ei.value.status == iqa.IQA_ERR_INVALID_ARG
+            after = iqa.iqa_plan_info(plan)
+            assert (after.total_units, after.config.unit_kpx, after.config.stages,
+                    after.config.threads) == (before.total_units, before.config.unit_kpx,
+                                              before.config.stages, before.config.threads)
+        iqa.iqa_plan_launch(plan, torch.cuda.current_stream())
+        iqa.iqa_wait(ctx, torch.cuda.current_stream(), 20_000_000)
+    finally:
+        iqa.iqa_plan_destroy(plan)
+    assert np.all(np.isfinite(b.results(0)[0]))
