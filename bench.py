@@ -903,7 +903,8 @@ def run_ours(args):
         pl, _keep = make_plan(nt)
         if args.tune_iters > 0:
             iqa.iqa_plan_autotune(pl, stream, args.tune_iters)
-        ms = _time_plan(iqa, ctx, pl, stream, max(10, min(K, 200)), 3)
+        ms = _time_plan(iqa, ctx, pl, stream, max(10, min(K, 200)), 3,
+                        label="nt_sweep_%d" % nt)
         sweep[str(nt)] = round(max(10, min(K, 200)) * B * pair_bytes / (ms * 1e-3) / 1e9, 1)
         iqa.iqa_plan_destroy(pl)
 
