@@ -55,8 +55,8 @@ PROFILED_TRAFFIC = {
     "sources": ["paper_2501_10653_gb300/csrc/iqa_device.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream_f32.cu"],
-    "sha256": "4412710aea8450207c46b2b368d57e3f50ed87e39966d0f7e958bd0809f62586",
-    "bytes_per_launch": 1073811712 + 3404800,
+    "sha256": "a018e7f47bf3a2ee8b9081e2bfae0bd705d2ae9c8db7c685d10fdfd62c49ebac",
+    "bytes_per_launch": 1073826816 + 3371520,
     "pairs_per_launch": 32,
     "capture": "the timed launch itself (first launch in the headline_timed NVTX range, "
                "32 pairs, 456 CTAs of 160 threads)",
