@@ -858,9 +858,9 @@ iqa_status iqa_server_create(iqa_ctx *ctx, const iqa_server_config *cfg, iqa_ser
             std::lock_guard<std::mutex> g(ctx->cfg_mu);
             if (ctx->has_batch_cfg[cfg->dtype]) srv->kcfg = ctx->batch_cfg[cfg->dtype];
         }
-        // serving steps are latency-bound: units of 16K pixel pairs (half the
-        // batched form's 16-bit default) spread a small request over more CTAs
-        // (served p50 0.079 against 0.089 ms with 32K units)
+        // serving steps are latency-bound: units of 16K pixel pairs (a quarter
+        // of the batched form's 16-bit default) spread a small request over
+        // more CTAs (served p50 0.079 against 0.089 ms with 32K units)
         srv->kcfg.unit_kpx = 16;
         if (cfg->map_ctas_per_sm > 0) {
             TileConfig k = srv->kcfg;

@@ -94,7 +94,7 @@ def main():
     # batched plans whose units span several tile rows (explicit shapes)
     for N, NT, dt, th, kpx in ((1024, 16, "f32", 128, 32), (288, 16, "f32", 128, 32),
                                (2048, 32, "f32", 256, 64), (768, 16, "f16", 128, 32),
-                               (512, 8, "f32", 128, 64)):
+                               (512, 8, "f32", 128, 64), (2048, 64, "f32", 128, 64)):
         x, y = synth.mixed_batch_pair(1, N, dtype=dt)
         dx, dy = parity.to_device(x), parity.to_device(y)
         T = N // NT
