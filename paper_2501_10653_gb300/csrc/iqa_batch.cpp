@@ -99,7 +99,7 @@ static iqa_status plan_build(iqa_plan *pl, const TileConfig &cfg)
     pl->grid = stream_grid(ctx, cfg, units);
     // each CTA's first grab spans about head_bytes() of each image (at most
     // 8 units), counted on the first pair's units (the largest); one unit of
-    // 16K-64K pixel pairs alone is 32-256 KB
+    // 16K-128K pixel pairs alone is 32-256 KB
     if (n > 0) {
         const PairDesc &d0 = pl->h_table[0];
         const long long unit_bytes =
@@ -166,11 +166,13 @@ static iqa_status plan_capture(iqa_plan *pl)
 
 // Batched-kernel shape when nothing was tuned: the autotuner's usual choice on
 // GB300 (three CTAs per SM, each a 128-thread consumer group with a two-stage
-// ring of 16 KB per image), with units of 32K pixel pairs for FP32 and 64K for
-// 16-bit storage (128 KB of each image).  Measured on 32 N=2048 pairs, same
-// box: FP32 units of 32K against 16K stream 1.4% faster at N_T = 64 and 0.9%
-// at N_T = 16; 16-bit units of 64K against 32K 1.9% faster at N_T = 64 and
-// 1.3% at N_T = 32 (a unit row of 1024 pixels, 2 KB, instead of 512).
+// ring of 16 KB per image), with units of 32K pixel pairs for FP32 (128 KB of
+// each image) and 128K for 16-bit storage (256 KB).  Measured on 32 N=2048
+// pairs, same box: FP32 units of 32K against 16K stream 1.4% faster at
+// N_T = 64 and 0.9% at N_T = 16, and 64K or more no faster (128K: 0.6%
+// slower); 16-bit units of 64K against 32K 1.9% faster at N_T = 64 and 1.3% at
+// N_T = 32 (a unit row of 1024 pixels, 2 KB, instead of 512), and 128K another
+// 1.2% and 1.5% (two tile rows of 1024 pixels).
 TileConfig default_batch_config(iqa_dtype dtype)
 {
     TileConfig c;
@@ -179,7 +181,7 @@ TileConfig default_batch_config(iqa_dtype dtype)
     c.stages = 2;
     c.stage_kb = 16;
     c.ctas_per_sm = 3;
-    c.unit_kpx = elem_size(dtype) == 2 ? 64 : 32;
+    c.unit_kpx = elem_size(dtype) == 2 ? 128 : 32;
     return c;
 }
 
@@ -369,7 +371,7 @@ iqa_status iqa_plan_autotune(iqa_plan *plan, iqa_stream stream, int iters,
                               {2, 16, 3, 4},  {4, 16, 1, 16}, {8, 8, 1, 4},
                               {3, 8, 4, 4},   {2, 8, 4, 4},   {2, 16, 3, 16},
                               {2, 16, 3, 32}, {3, 16, 2, 32}, {2, 16, 3, 64},
-                              {4, 8, 3, 64}};
+                              {4, 8, 3, 64},  {2, 16, 3, 128}};
     iqa_status s = IQA_OK;
     for (int th : threads_c) {
         for (const auto &sh : shape_c) {

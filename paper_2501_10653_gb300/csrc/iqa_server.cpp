@@ -858,7 +858,7 @@ iqa_status iqa_server_create(iqa_ctx *ctx, const iqa_server_config *cfg, iqa_ser
             std::lock_guard<std::mutex> g(ctx->cfg_mu);
             if (ctx->has_batch_cfg[cfg->dtype]) srv->kcfg = ctx->batch_cfg[cfg->dtype];
         }
-        // serving steps are latency-bound: units of 16K pixel pairs (a quarter
+        // serving steps are latency-bound: units of 16K pixel pairs (an eighth
         // of the batched form's 16-bit default) spread a small request over
         // more CTAs (served p50 0.079 against 0.089 ms with 32K units)
         srv->kcfg.unit_kpx = 16;
