@@ -921,7 +921,7 @@ def run_ours(args):
         tuned16 = (iqa.iqa_plan_autotune(pl16, stream, args.tune_iters).as_dict()
                    if args.tune_iters > 0 else None)
         K16 = max(10, min(K, 2000))
-        ms = _time_plan(iqa, ctx, pl16, stream, K16, 3)
+        ms = _time_plan(iqa, ctx, pl16, stream, K16, 3, label="storage_" + name)
         iqa.iqa_plan_destroy(pl16)
         # twice the pairs per launch (a second copy of each), so that a launch
         # moves the same bytes as the FP32 step: separates the per-launch cost
