@@ -212,7 +212,9 @@ __device__ __forceinline__ void write_tile_desc(const PairDesc &d, long long t, 
 // Dynamic shared memory layout: [stages][2][stage_bytes] ring, then the
 // 2*stages mbarriers, the per-stage slots (first tile of the stage's unit
 // within its pair, -1 at the end of work; the pair's index), the reduction scratch
-// red[4][CT] and part[kMaxTX*4], and the abort flag.  Host:
+// red[4][2 * CT] (the segmented form's per-tile-row slots; reduce_unit views
+// its first 4 * CT floats as red[4][CT]) and part[kMaxTX*4], and the abort
+// flag.  Host:
 // stream_smem_bytes().
 template <typename T, int CT, bool DO_A, bool DO_B>
 __global__ void __launch_bounds__(CT + 32, 1)
@@ -228,7 +230,8 @@ __global__ void __launch_bounds__(CT + 32, 1)
     long long *stage_unit = reinterpret_cast<long long *>(empty + S);
     int *stage_pair = reinterpret_cast<int *>(stage_unit + S);
     float(*red)[CT] = reinterpret_cast<float(*)[CT]>(stage_unit + 2 * S);
-    float *part = reinterpret_cast<float *>(red + 4);
+    float(*rows)[2 * CT] = reinterpret_cast<float(*)[2 * CT]>(red);
+    float *part = reinterpret_cast<float *>(rows + 4);
     int *abort_flag = reinterpret_cast<int *>(part + kMaxTX * 4);
 
     const PairDesc *descs = sp.descs ? sp.descs : &sp.one_pair;
@@ -534,8 +537,8 @@ __global__ void __launch_bounds__(CT + 32, 1)
                 // 2 that began this unit)
                 cr = 0;
                 const float acc[4] = {ka.value(), kb.value(), kx.value(), ky.value()};
-                if (IQA_CHECK((r + 1) * spr <= CT))
-                    segmented_partials<CT>(acc, d->TX, d->LPU, d->LPT, r * spr, red);
+                if (IQA_CHECK((r + 1) * spr <= 2 * CT))
+                    segmented_partials<2 * CT>(acc, d->TX, d->LPU, d->LPT, r * spr, rows);
                 ka = Kahan();
                 kb = Kahan();
                 kx = Kahan();
@@ -550,13 +553,13 @@ __global__ void __launch_bounds__(CT + 32, 1)
                 const int TX = d->TX, T = d->T, RH = d->RH;
                 const int groups = spr / TX;
                 const bool out_ok = IQA_CHECK(t0 + (long long)(RH - 1) * T + TX <=
-                                              (long long)T * T && RH * spr <= CT);
+                                              (long long)T * T && RH * spr <= 2 * CT);
                 for (int tl = tid; tl < RH * TX && out_ok; tl += CT) {
                     const int rr = tl / TX, tx = tl - rr * TX;
                     float sm[4] = {0.0f, 0.0f, 0.0f, 0.0f};
                     for (int g = 0; g < groups; ++g) {
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) sm[k] += red[k][rr * spr + g * TX + tx];
+                        for (int k = 0; k < 4; ++k) sm[k] += rows[k][rr * spr + g * TX + tx];
                     }
                     write_tile_desc(*d, t0 + (long long)rr * T + tx, sm[0], sm[1], sm[2],
                                     sm[3]);
@@ -583,7 +586,7 @@ __global__ void __launch_bounds__(CT + 32, 1)
 inline size_t stream_smem_bytes(int stages, int stage_bytes, int ct)
 {
     return (size_t)stages * 2 * stage_bytes + (size_t)2 * stages * 8 + (size_t)2 * stages * 8 +
-           (size_t)4 * ct * 4 + (size_t)kMaxTX * 4 * 4 + 16;
+           (size_t)8 * ct * 4 + (size_t)kMaxTX * 4 * 4 + 16;
 }
 
 }  // namespace iqa

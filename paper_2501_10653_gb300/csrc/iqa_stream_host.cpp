@@ -81,7 +81,7 @@ bool stream_config_valid(int N, int NT, iqa_dtype dtype, const TileConfig &c,
     if (c.RH < 1 || T % c.RH) return fail("tile rows per unit must divide N/NT");
     if (c.RH > 1 && !segmented_reduce(c.TX, LPU, NT / V))
         return fail("several tile rows per unit need the segmented reduction");
-    if (c.RH > 1 && c.RH * segmented_slots(c.threads, c.TX, LPU) > c.threads)
+    if (c.RH > 1 && c.RH * segmented_slots(c.threads, c.TX, LPU) > 2 * c.threads)
         return fail("too many tile rows per unit for the reduction slots");
     if (!chunk_rows(NT, BW, es, c.stage_kb * 1024))
         return fail("a unit row does not fit one stage");
@@ -120,7 +120,7 @@ int stream_tiles_across(int N, int NT, iqa_dtype dtype, int threads, long long u
 
 // Most tile rows down a unit of TX tiles across (dividing N / NT) whose
 // pixel pairs stay within unit_px and whose per-row reduction slots fit the
-// consumer threads; 1 where the unit does not take the segmented reduction.
+// kernel's 2 * threads; 1 where the unit does not take the segmented reduction.
 int stream_unit_rows(int N, int NT, iqa_dtype dtype, int threads, int TX, long long unit_px)
 {
     const int V = 16 / elem_size(dtype);
@@ -128,7 +128,7 @@ int stream_unit_rows(int N, int NT, iqa_dtype dtype, int threads, int TX, long l
     if (!segmented_reduce(TX, LPU, LPT)) return 1;
     const int spr = segmented_slots(threads, TX, LPU);
     int best = 1;
-    for (int rh = 2; rh * spr <= threads && (long long)rh * TX * NT * NT <= unit_px; ++rh)
+    for (int rh = 2; rh * spr <= 2 * threads && (long long)rh * TX * NT * NT <= unit_px; ++rh)
         if (T % rh == 0) best = rh;
     return best;
 }

@@ -314,18 +314,20 @@ def _plan_with_shape(ctx, batch, shape, flags=0, dtype_code=0, launches=1):
 
 
 # (N, N_T, storage, threads, unit_kpx, tiles across TX, tile rows per unit RH):
-# a unit of RH > 1 tile rows keeps per-tile-row partials and reduces them at
-# its end.  Cases: RH 1 / 2 / 4 at the same TX (128-vector unit rows); RH 9 on
-# 8-vector unit rows (a warp spans four unit rows); 3-D boxes (1024-element
-# unit rows); 16-bit storage.
+# a unit of RH > 1 tile rows keeps per-tile-row partials (up to twice the
+# consumer threads of reduction slots) and reduces them at its end.  Cases: RH
+# 1 / 2 / 4 (128-vector unit rows); RH 18 on 8-vector unit rows (a warp spans
+# four unit rows; 144 slots, more than the 128 threads); 3-D boxes
+# (1024-element unit rows); 16-bit storage (RH 4 with 256 slots).
 MULTI_ROW = [
     (1024, 16, "f32", 128, 8, 32, 1),
     (1024, 16, "f32", 128, 16, 32, 2),
     (1024, 16, "f32", 128, 32, 32, 4),
-    (288, 16, "f32", 128, 32, 2, 9),
+    (288, 16, "f32", 128, 32, 2, 18),
     (2048, 32, "f32", 256, 64, 32, 2),
-    (768, 16, "f16", 128, 32, 16, 2),
-    (512, 8, "f32", 128, 64, 64, 2),
+    (768, 16, "f16", 128, 32, 16, 4),
+    (1024, 16, "f16", 128, 128, 64, 4),
+    (512, 8, "f32", 128, 64, 64, 4),
 ]
 
 
@@ -346,13 +348,14 @@ def test_multi_row_units_against_oracle(ctx, orc, N, NT, dt, threads, kpx, TX, R
 
 def test_multi_row_units_change_no_bit(ctx):
     """At the same unit width a thread sums the same columns of the same chunks
-    whatever the tile rows per unit, so 1, 2 and 4 rows give the same bits,
-    stream-ordered and as independent launches back to back."""
+    whatever the tile rows per unit, so 1, 2, 4 and 8 rows (256 reduction
+    slots) give the same bits, stream-ordered and as independent launches back
+    to back."""
     from paper_2501_10653_gb300 import iqa
     b = Batch([(1024, 16), (512, 16)], seed=52)
     _plan_with_shape(ctx, b, {"unit_kpx": 8})
     want = [b.results(i) for i in range(2)]
-    for kpx in (16, 32):
+    for kpx in (16, 32, 64):
         for flags, launches in ((0, 1), (iqa.IQA_PLAN_INDEPENDENT | iqa.IQA_PLAN_GRAPH, 3)):
             _plan_with_shape(ctx, b, {"unit_kpx": kpx}, flags=flags, launches=launches)
             for i in range(2):
