@@ -55,8 +55,8 @@ PROFILED_TRAFFIC = {
     "sources": ["paper_2501_10653_gb300/csrc/iqa_device.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream.cuh",
                 "paper_2501_10653_gb300/csrc/iqa_stream_f32.cu"],
-    "sha256": "a018e7f47bf3a2ee8b9081e2bfae0bd705d2ae9c8db7c685d10fdfd62c49ebac",
-    "bytes_per_launch": 1073826816 + 3371520,
+    "sha256": "2daea2031a454c9b26fa4d2cc8a5d7f5876e823efeb5ddc2016b6617d6c50eae",
+    "bytes_per_launch": 1073827840 + 3504640,
     "pairs_per_launch": 32,
     "capture": "the timed launch itself (first launch in the headline_timed NVTX range, "
                "32 pairs, 456 CTAs of 160 threads)",
