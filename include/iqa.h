@@ -317,7 +317,8 @@ typedef struct iqa_plan iqa_plan;
  * with the values this launch writes.  The plan's own previous launch
  * qualifies (a plan's results repeat bit for bit), and so does another
  * plan's launch over other outputs.  Each CTA then starts copying its first
- * grab (about 256 KB of each image) while that kernel drains, instead of
+ * grab (about 256 KB of each image, 512 KB for 16-bit storage) while that
+ * kernel drains, instead of
  * after it completes; every other access, and the launch's completion, still
  * follow it.  Breaking the
  * promise gives wrong maps, not a fault.  Effective for direct launches (a
@@ -329,7 +330,11 @@ typedef struct iqa_plan iqa_plan;
  * map per image, uploads the work-list descriptors to device memory owned by
  * the plan, and (with IQA_PLAN_GRAPH) captures the launch in a CUDA graph.
  * The pair array is copied; the buffers it points to must stay valid while
- * the plan is used.  Synchronous.
+ * the plan is used.  Synchronous.  The launch shape is the one the context's
+ * last iqa_plan_autotune picked for this dtype, else the default: 128
+ * consumer threads, 3 CTAs per SM, 2 stages of 16 KB per image, units of 32K
+ * pixel pairs for FP32 and 128K for 16-bit storage (iqa_plan_set_config sets
+ * another).
  * Errors: IQA_ERR_INVALID_ARG (bad pair, shape, dtype, constants),
  * IQA_ERR_UNSUPPORTED (a pair the TMA kernel cannot stream: unaligned images,
  * NT not a multiple of 16 bytes or above 256), IQA_ERR_NOMEM, IQA_ERR_CUDA.
