@@ -68,7 +68,9 @@ static iqa_status check_pair(iqa_ctx *ctx, const iqa_pair &p, iqa_dtype dtype, i
 // N_T = 32 / 64 a further +1% but loses 4% on FP32 N_T = 32 and 64 (the
 // static grabs then unbalance the CTAs), so 16-bit storage takes 512 KB.
 // (Capping the static grabs at a quarter of the work instead cost FP16 up to
-// 0.8% at N = 1024 ... 4096.)
+// 0.8% at N = 1024 ... 4096.)  With 16-bit units of 128K pixel pairs (256 KB
+// of each image) 512 KB is still best: 256 KB lost 2.5% and 1 MB 6% at
+// N_T = 32 and 64.
 static long long head_bytes(iqa_dtype dtype) { return elem_size(dtype) == 2 ? 524288 : 262144; }
 
 // (Re)build the descriptor table for cfg and upload it.
