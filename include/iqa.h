@@ -380,8 +380,9 @@ iqa_status iqa_plan_set_config(iqa_plan *plan, const iqa_launch_config *cfg);
 
 /*
  * Autotuner: times the plan under several launch shapes of the persistent
- * kernel (consumer threads, ring depth, stage size, CTAs per SM), `iters`
- * launches each on `stream` (synchronising it), keeps the fastest, re-captures
+ * kernel (consumer threads, ring depth, stage size, CTAs per SM, unit size),
+ * `iters` launches each on `stream` (synchronising it), re-times the three
+ * fastest with 3 * iters launches each, keeps the fastest of those, re-captures
  * the graph, and remembers the shape for later plans of the same dtype on
  * this context.  *best_out (nullable) receives it.
  */

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <utility>
 #include <vector>
 
 #include "iqa.h"
@@ -365,7 +366,6 @@ iqa_status iqa_plan_autotune(iqa_plan *plan, iqa_stream stream, int iters,
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    float best_ms = 1e30f;
     TileConfig best = keep;
     const int threads_c[] = {128, 256};
     // {stages, stage_kb, ctas_per_sm, unit_kpx}
@@ -376,6 +376,26 @@ iqa_status iqa_plan_autotune(iqa_plan *plan, iqa_stream stream, int iters,
                               {2, 16, 3, 32}, {3, 16, 2, 32}, {2, 16, 3, 64},
                               {4, 8, 3, 64},  {2, 16, 3, 128}};
     iqa_status s = IQA_OK;
+    // time of `n` back-to-back launches of the plan built for c, after one
+    // untimed launch; < 0 when the plan cannot take c (s is set on a CUDA error)
+    const auto time_shape = [&](const TileConfig &c, int n) -> float {
+        if (plan_build(plan, c) != IQA_OK) return -1.0f;
+        cudaError_t e = plan_launch_direct(plan, (cudaStream_t)stream);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, (cudaStream_t)stream);
+        for (int i = 0; i < n && e == cudaSuccess; ++i)
+            e = plan_launch_direct(plan, (cudaStream_t)stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, (cudaStream_t)stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            s = cuda_fail(ctx, e, "autotune launch");
+            return -1.0f;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    // first pass: every shape, `iters` launches each
+    std::vector<std::pair<float, TileConfig>> timed;
     for (int th : threads_c) {
         for (const auto &sh : shape_c) {
             TileConfig c = keep;
@@ -384,25 +404,26 @@ iqa_status iqa_plan_autotune(iqa_plan *plan, iqa_stream stream, int iters,
             c.stage_kb = sh[1];
             c.ctas_per_sm = sh[2];
             c.unit_kpx = sh[3];
-            if (plan_build(plan, c) != IQA_OK) continue;
-            cudaError_t e = plan_launch_direct(plan, (cudaStream_t)stream);  // warm-up
-            if (e == cudaSuccess) e = cudaEventRecord(e0, (cudaStream_t)stream);
-            for (int i = 0; i < iters && e == cudaSuccess; ++i)
-                e = plan_launch_direct(plan, (cudaStream_t)stream);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, (cudaStream_t)stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            if (e != cudaSuccess) {
-                s = cuda_fail(ctx, e, "autotune launch");
-                break;
-            }
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = c;
-            }
+            const float ms = time_shape(c, iters);
+            if (s != IQA_OK) break;
+            if (ms >= 0.0f) timed.emplace_back(ms, c);
         }
         if (s != IQA_OK) break;
+    }
+    // second pass: the three fastest again, 3 * iters launches each, slowest
+    // first, the fastest of them kept (shapes within a percent of each other
+    // are ordered by more than one short sample)
+    std::stable_sort(timed.begin(), timed.end(),
+                     [](const std::pair<float, TileConfig> &a,
+                        const std::pair<float, TileConfig> &b) { return a.first < b.first; });
+    const int finalists = (int)std::min<size_t>(3, timed.size());
+    float best_ms = 1e30f;
+    for (int k = finalists - 1; k >= 0 && s == IQA_OK; --k) {
+        const float ms = time_shape(timed[k].second, 3 * iters);
+        if (ms >= 0.0f && ms < best_ms) {
+            best_ms = ms;
+            best = timed[k].second;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
