@@ -1,8 +1,11 @@
 """Parity at the workloads' full sizes, in the launch configurations that
 bench.py times (needs a GPU):
 
-* 32 distinct N=2048, N_T=64 FP32 pairs in one autotuned, graph-captured
-  persistent launch, launched back to back: every tile against the oracle;
+* 32 distinct N=2048, N_T=64 FP32 pairs in one autotuned persistent launch
+  of an independent plan, launched back to back: every tile against the
+  oracle;
+* the same 32 pairs at N_T = 16, 32, 128, 256, and stored in FP16 / BF16
+  (the bench's N_T sweep and 16-bit steps): every tile of four pairs;
 * the 64-pair mixed batch (N up to 8192, 7.9 GB) rendered on the device,
   one autotuned launch: sampled tiles;
 * 16 pairs at N=8192, N_T=64 in FP16 and BF16, one launch: sampled tiles;
@@ -11,6 +14,7 @@ bench.py times (needs a GPU):
 Sampled tiles are checked against the oracle on pixel windows that the host
 mirror of the device generator (synth.render_epoch_window) makes, bit for
 bit, so no oracle input comes from the CUDA path."""
+import functools
 import math
 
 import numpy as np
@@ -31,6 +35,12 @@ def ctx():
     h = iqa.iqa_create(0, 0)
     yield h
     iqa.iqa_destroy(h)
+
+
+@functools.lru_cache(maxsize=None)
+def _paper_pairs(dt, count=32):
+    """The headline's seeded paper-scale pairs, stored as dt on the host."""
+    return tuple(synth.paper_pair(pair_index=i, dtype=dt) for i in range(count))
 
 
 def _picks(T, rng, k):
@@ -74,6 +84,36 @@ def test_headline_configuration_every_tile(ctx, orc):
     for (x, y), (lm, am) in zip(host, outs):
         want = parity.oracle_maps(orc, x, y, NT, PARAMS)
         parity.assert_parity((lm.cpu().numpy(), am.cpu().numpy(), None), want, PARAMS)
+
+
+@pytest.mark.parametrize("NT,dt", [(16, "f32"), (32, "f32"), (128, "f32"), (256, "f32"),
+                                   (64, "f16"), (16, "f16"), (64, "bf16")])
+def test_sweep_and_16bit_steps_full_size(ctx, orc, NT, dt):
+    """bench.py's N_T sweep and 16-bit steps: the headline's 32 pairs at
+    another N_T (units of several tile rows at N_T = 16 and 32), or rounded
+    to 16 bits (units of 128K pixel pairs), one autotuned independent plan
+    launched back to back; every tile of four of the pairs against the
+    oracle on the stored pixels."""
+    import torch
+    from paper_2501_10653_gb300 import iqa
+    N, B = 2048, 32
+    T = N // NT
+    code = {"f32": iqa.IQA_F32, "f16": iqa.IQA_F16, "bf16": iqa.IQA_BF16}[dt]
+    # rounded to the storage type on the host (BF16 as bit patterns), so the
+    # oracle reads the same stored pixels as the kernel
+    host = _paper_pairs(dt, B)
+    dev = [(parity.to_device(x), parity.to_device(y)) for x, y in host]
+    outs = [(torch.full((T * T,), float("nan"), device="cuda"),
+             torch.full((T * T,), float("nan"), device="cuda")) for _ in range(B)]
+    pairs = [iqa.make_pair(d[0], d[1], N, NT, o[0], o[1]) for d, o in zip(dev, outs)]
+    _plan_run(ctx, pairs, code, 2, 5, iqa.IQA_PLAN_INDEPENDENT)
+    for i in (0, 13, 22, B - 1):
+        x, y = host[i]
+        want = parity.oracle_maps(orc, x, y, NT, PARAMS)
+        lm, am = outs[i]
+        parity.assert_parity((lm.cpu().numpy(), am.cpu().numpy(), None), want, PARAMS)
+    del dev, outs
+    torch.cuda.empty_cache()
 
 
 def test_mixed_batch_full_size_sampled(ctx, orc):
