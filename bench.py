@@ -454,6 +454,32 @@ def small_pair_report(iqa, ctx, params, stream):
         e1.record(stream)
     torch.cuda.synchronize()
     b2b = e0.elapsed_time(e1) * 1e3 / 400
+
+    # the same calls captured in a CUDA graph (no host launch cost), stream
+    # ordered and as independent calls (each call's neighbours write other
+    # maps, so the promise holds)
+    def graph_us(independent):
+        G = 8 * C
+        iqa.iqa_set_option(ctx, iqa.IQA_OPT_INDEPENDENT_CALLS, independent)
+        try:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                for i in range(G):
+                    fn(i)
+        finally:
+            iqa.iqa_set_option(ctx, iqa.IQA_OPT_INDEPENDENT_CALLS, 0)
+        with torch.cuda.stream(stream):
+            g.replay()
+            g0 = torch.cuda.Event(enable_timing=True)
+            g1 = torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            for _ in range(10):
+                g.replay()
+            g1.record(stream)
+        torch.cuda.synchronize()
+        return g0.elapsed_time(g1) * 1e3 / (10 * G)
+    graph_b2b = graph_us(0)
+    graph_indep = graph_us(1)
     return {"workload": "N=256 N_T=64 FP32 (16 tiles), 10 sources FWHM 3 px, flux 0.01..1, "
                         "noise sigma 1e-3, 3 faintest dropped, seed 0; one iqa_both call "
                         "per pair",
@@ -461,6 +487,8 @@ def small_pair_report(iqa, ctx, params, stream):
             "single_launch_us_mean": round(mean, 3),
             "back_to_back_us_per_pair": round(b2b, 3),
             "back_to_back_GBs": round(2 * N * N * 4 / (b2b * 1e-6) / 1e9, 1),
+            "graph_back_to_back_us_per_pair": round(graph_b2b, 3),
+            "graph_independent_calls_us_per_pair": round(graph_indep, 3),
             "launch": iqa.iqa_get_config(ctx, iqa.IQA_F32, N, NT, iqa.MAPS_BOTH).as_dict(),
             "_maps": (x, y, lm[0].cpu().numpy().astype(np.float64),
                       am[0].cpu().numpy().astype(np.float64))}
