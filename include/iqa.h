@@ -372,7 +372,9 @@ iqa_status iqa_plan_info(const iqa_plan *plan, iqa_plan_stats *out);
  * Sets the plan's launch shape (variant 1: threads, stages, stage_kb,
  * ctas_per_sm, unit_kpx in 1..1024; the per-pair unit follows from unit_kpx),
  * rebuilds its descriptors and re-captures its graph.  Synchronous; no launch
- * of the plan may be running.  On error the plan keeps its previous shape.
+ * of the plan may be running.  On error the plan keeps its previous shape
+ * (unless restoring it fails with IQA_ERR_CUDA, after which the plan can only
+ * be destroyed).
  * Errors: IQA_ERR_INVALID_ARG (not variant 1, unit_kpx out of range, or a
  * shape some pair of the plan cannot take), IQA_ERR_CUDA.
  */

@@ -343,14 +343,17 @@ iqa_status iqa_plan_set_config(iqa_plan *plan, const iqa_launch_config *cfg)
     c.unit_kpx = cfg->unit_kpx;
     iqa_status s = plan_build(plan, c);
     if (s != IQA_OK) {
-        // the plan keeps its previous shape (and the error message this one set)
+        // back to the previous shape, keeping the error message of this one;
+        // if even that fails (a CUDA error), its status is returned and the
+        // plan can only be destroyed
         std::string msg;
         {
             std::lock_guard<std::mutex> g(ctx->err_mu);
             msg = ctx->last_error;
         }
-        plan_build(plan, keep);
-        set_error(ctx, "%s", msg.c_str());
+        const iqa_status r = plan_build(plan, keep);
+        if (r == IQA_OK) set_error(ctx, "%s", msg.c_str());
+        else s = r;
     }
     if (s == IQA_OK && plan->exec) s = plan_capture(plan);
     cudaSetDevice(prev);
