@@ -123,8 +123,8 @@ iqa_status iqa_create(iqa_ctx **out, int device, size_t hbm_budget_bytes);
 void iqa_destroy(iqa_ctx *ctx);
 
 /*
- * One-line reason for the latest failed call on ctx (or of iqa_create when
- * ctx is NULL).  The string belongs to the library and stays valid until the
+ * One-line reason for the latest failed call on ctx (or, when ctx is NULL,
+ * of iqa_create and the calls that take no context).  The string belongs to the library and stays valid until the
  * next call on the same context.
  */
 const char *iqa_last_error(const iqa_ctx *ctx);
@@ -379,6 +379,20 @@ iqa_status iqa_plan_info(const iqa_plan *plan, iqa_plan_stats *out);
  * shape some pair of the plan cannot take), IQA_ERR_CUDA.
  */
 iqa_status iqa_plan_set_config(iqa_plan *plan, const iqa_launch_config *cfg);
+
+/*
+ * The unit that a plan of launch shape `cfg` (variant 1) streams one pair of
+ * side N and tile side NT in, by the rules iqa_plan_create and
+ * iqa_plan_set_config apply: *tiles_across whole tiles across (dividing
+ * N/NT), *tile_rows tile rows down (dividing N/NT), and *units units in the
+ * pair's work list, (N/NT/tile_rows) * (N/NT/tiles_across), taken in
+ * row-major order of their first tiles.  A host-only query: needs no GPU and
+ * no context.
+ * Errors: IQA_ERR_INVALID_ARG (null argument, bad dtype, N, NT or shape, or a
+ * shape the pair cannot take); the reason is in iqa_last_error(NULL).
+ */
+iqa_status iqa_plan_unit_shape(iqa_dtype dtype, int N, int NT, const iqa_launch_config *cfg,
+                               int *tiles_across, int *tile_rows, long long *units);
 
 /*
  * Autotuner: times the plan under several launch shapes of the persistent

@@ -360,6 +360,46 @@ iqa_status iqa_plan_set_config(iqa_plan *plan, const iqa_launch_config *cfg)
     return s;
 }
 
+iqa_status iqa_plan_unit_shape(iqa_dtype dtype, int N, int NT, const iqa_launch_config *cfg,
+                               int *tiles_across, int *tile_rows, long long *units)
+{
+    if (!cfg || !tiles_across || !tile_rows || !units) {
+        set_error(nullptr, "need cfg and the three outputs");
+        return IQA_ERR_INVALID_ARG;
+    }
+    if (!dtype_ok(dtype)) {
+        set_error(nullptr, "unknown dtype %d", (int)dtype);
+        return IQA_ERR_INVALID_ARG;
+    }
+    if (check_shape(nullptr, N, NT) != IQA_OK) return IQA_ERR_INVALID_ARG;
+    const int V = 16 / elem_size(dtype);
+    if (NT % V || NT > 256) {
+        set_error(nullptr, "the batched kernel needs NT a multiple of 16 bytes, at most 256 "
+                           "(NT=%d)", NT);
+        return IQA_ERR_INVALID_ARG;
+    }
+    if (cfg->variant != 1 || cfg->unit_kpx < 1 || cfg->unit_kpx > 1024) {
+        set_error(nullptr, "a plan takes a variant 1 shape with unit_kpx in 1..1024");
+        return IQA_ERR_INVALID_ARG;
+    }
+    TileConfig c = default_batch_config(dtype);
+    c.threads = cfg->threads;
+    c.stages = cfg->stages;
+    c.stage_kb = cfg->stage_kb;
+    c.ctas_per_sm = cfg->ctas_per_sm;
+    c.unit_kpx = cfg->unit_kpx;
+    stream_unit_shape(c, N, NT, dtype);
+    std::string why;
+    if (!stream_config_valid(N, NT, dtype, c, &why)) {
+        set_error(nullptr, "N=%d NT=%d: %s", N, NT, why.c_str());
+        return IQA_ERR_INVALID_ARG;
+    }
+    *tiles_across = c.TX;
+    *tile_rows = c.RH;
+    *units = pair_units(N, NT, c);
+    return IQA_OK;
+}
+
 iqa_status iqa_plan_autotune(iqa_plan *plan, iqa_stream stream, int iters,
                              iqa_launch_config *best_out)
 {

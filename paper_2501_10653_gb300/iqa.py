@@ -173,6 +173,8 @@ def _declare(lib):
         "iqa_plan_info": ([_vp, P(iqa_plan_stats)], _st),
         "iqa_plan_autotune": ([_vp, _vp, _i, P(iqa_launch_config)], _st),
         "iqa_plan_set_config": ([_vp, P(iqa_launch_config)], _st),
+        "iqa_plan_unit_shape": ([_i, _i, _i, P(iqa_launch_config), P(ctypes.c_int),
+                                 P(ctypes.c_int), P(ctypes.c_longlong)], _st),
         "iqa_batch_noalloc": ([P(iqa_pair), _i, _i, P(iqa_params), _vp], _st),
         "iqa_merge": ([_vp, _vp, _i, _i, P(iqa_params), _vp, _vp, _vp, _vp], _st),
         "iqa_both_host_many": ([_vp, P(iqa_host_pair), _i, _i, P(iqa_params)], _st),
@@ -383,6 +385,21 @@ def iqa_plan_set_config(plan, cfg):
         full.update(cfg)
         cfg = iqa_launch_config(**full)
     _check(plan.ctx, lib().iqa_plan_set_config(plan.handle, ctypes.byref(cfg)))
+
+
+def iqa_plan_unit_shape(dtype, N, NT, cfg):
+    """(tiles_across, tile_rows, units) of one pair in a plan of shape cfg (an
+    iqa_launch_config, or a dict of its variant 1 fields); host-only."""
+    if isinstance(cfg, dict):
+        full = {"variant": 1, "threads": 128, "ilp": 0, "tiles_across": 0, "split": 1,
+                "vector": 1, "stages": 2, "stage_kb": 16, "ctas_per_sm": 3, "unit_kpx": 32}
+        full.update(cfg)
+        cfg = iqa_launch_config(**full)
+    tx, rh, units = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+    _check(None, lib().iqa_plan_unit_shape(int(dtype), int(N), int(NT), ctypes.byref(cfg),
+                                           ctypes.byref(tx), ctypes.byref(rh),
+                                           ctypes.byref(units)))
+    return tx.value, rh.value, units.value
 
 
 def iqa_plan_autotune(plan, stream=None, iters=5):
